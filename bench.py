@@ -1,0 +1,296 @@
+#!/usr/bin/env python3
+"""Throughput of the lambda(omega)-mapped triangular kernels on one GB300.
+
+Default workload: the high-dimensional EDM, N = 65536 points of d = 128 FP32
+features drawn N(0,1) with 1% duplicated rows, every pair i >= j written to a
+packed lower triangle (2,147,516,416 distances, 8.59 GB).  A step is one full
+tri_edm call over that input (all kernels of the chosen precision path); the
+metric is pairs per second.  Beside it the line carries the bounding-box map
+on the same input and GPU (the paper's improvement factor I = t_BB / t_lambda),
+the FP32 and tensor-core arms, the roofline of the dominant kernel, an
+end-to-end figure through host buffers, and the CPU oracle timed on a bounded
+sample on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--prec fp32|bf16x3|bf16x6]
+
+With N > 1 (torchrun), every rank runs its own full instance of the workload
+(weak scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PTS, D_FEAT, DUP = 65536, 128, 0.01
+WORKLOAD = "edm_n65536_d128_normal_dup1pct"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+NUM_SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK), "fallback"
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+# ----------------------------------------------------------- clocks --------
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------ reference arm -------
+def cpu_oracle_sample(x: np.ndarray, target_s: float = 12.0):
+    """Time the CPU oracle on a band of full rows at the end of the triangle.
+
+    Returns (pairs/s, threads, sample description)."""
+    import oracle
+    n = x.shape[0]
+    probe = 64
+    t0 = time.perf_counter()
+    oracle.edm_rows(x, n - probe, n)
+    dt = time.perf_counter() - t0
+    pairs_probe = (n * (n + 1) - (n - probe) * (n - probe + 1)) // 2
+    rate = pairs_probe / max(dt, 1e-9)
+    rows = int(max(probe, min(n, target_s * rate / n)))
+    r0 = n - rows
+    t0 = time.perf_counter()
+    oracle.edm_rows(x, r0, n)
+    dt = time.perf_counter() - t0
+    pairs = (n * (n + 1) - r0 * (r0 + 1)) // 2
+    return pairs / dt, oracle.threads(), f"rows [{r0}, {n}) of the triangle: {pairs} pairs in {dt:.2f} s"
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    from paper_1609_01490_gb300 import inputs
+    x = inputs.edm_normal_points(N_PTS, D_FEAT, seed=1609, dup_frac=DUP)
+    total_pairs = N_PTS * (N_PTS + 1) // 2
+    vals = []
+    for s in range(args.warmup + args.steps):
+        rate, thr, sample = cpu_oracle_sample(x, target_s=8.0)
+        if s >= args.warmup:
+            vals.append(rate)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": "pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_pairs / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP,
+                   "note": "CPU oracle (FP64 direct differences), each step a bounded band of rows"},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": thr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- our arm -----
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3", "bf16x6"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1609_01490_gb300 import inputs
+    from paper_1609_01490_gb300 import tri
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prec = {"fp32": tri.FP32, "bf16x3": tri.BF16X3, "bf16x6": tri.BF16X6}[args.prec]
+    x_host = inputs.edm_normal_points(N_PTS, D_FEAT, seed=1609 + rank, dup_frac=DUP)
+    P = N_PTS * (N_PTS + 1) // 2
+    x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty(P, dtype=torch.float32, device=dev)
+    ws_bytes = tri.tri_edm_workspace_size(N_PTS, D_FEAT, prec)
+    ws = torch.empty(max(ws_bytes, 16), dtype=torch.uint8, device=dev)
+    flagged = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(map_id, out_t=out, x_t=x):
+        tri.tri_edm(x_t, out_t, map=map_id, rho=16, reg=4, prec=prec,
+                    workspace=ws if ws_bytes else None, n_flagged=flagged if prec != tri.FP32 else None)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return ev0.elapsed_time(ev1) / k  # ms per step
+
+    # ---- headline: lambda map, timed region with clock sampling
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    for _ in range(args.warmup):
+        step(tri.MAP_LAMBDA)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ms_lambda = timed(lambda: step(tri.MAP_LAMBDA), args.steps, 0)
+    clocks = sampler.stop()
+    ms_t = torch.tensor([ms_lambda], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_step = float(ms_t.item())
+    value = world * P / (ms_step * 1e-3)
+
+    # ---- bounding box on the same input (the paper's I = t_BB / t_lambda)
+    ms_bb = timed(lambda: step(tri.MAP_BB), max(3, args.steps // 2), 2)
+
+    # ---- roofline of the dominant kernel (one kernel per FP32 step)
+    peaks, peak_src = load_peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0))
+    if prec == tri.FP32:
+        flops = 3.0 * D_FEAT * P  # sub, mul, add per feature and pair
+        achieved = flops / (ms_step * 1e-3) / 1e12
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "edm_kernel<lambda,16,4>", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz (derived)"}
+    else:
+        roof = None
+
+    # ---- end to end through host buffers: pinned H2D of x, tri_edm, D2H of the triangle
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        oh = torch.empty(P, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            x.copy_(xh, non_blocking=True)
+            step(tri.MAP_LAMBDA)
+            oh.copy_(out, non_blocking=True)
+
+        ms_e2e = timed(e2e_step, max(2, min(args.steps, 5)), 1)
+        e2e = {"value": world * P / (ms_e2e * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": xh.numel() * 4,
+               "d2h_bytes_per_step": oh.numel() * 4}
+        del oh, xh
+
+    line = {
+        "metric": "pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "bf16x6": "bf16"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP, "map": "lambda", "rho": 16,
+                   "reg": 4, "prec": args.prec, "pairs_per_step": P,
+                   "l2": "each step writes the 8.59 GB triangle (> 129 MB L2), which flushes L2 between steps"},
+        "bb": {"ms_per_step": ms_bb, "value": world * P / (ms_bb * 1e-3), "I_bb_over_lambda": ms_bb / ms_step},
+        "clocks": clocks,
+        "gpu_launches": args.steps * 1,
+        "roofline": roof,
+        "peaks": {"source": peak_src},
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu:
+        rate, thr, sample = cpu_oracle_sample(x_host)
+        line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": thr, "kind": "oracle", "sample": sample,
+                                "host_cores": host_cores()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * tri.h -- C ABI of libtri.so: GPU kernels on triangular and tetrahedral
+ * domains whose grids are mapped onto the domain by the block-space map
+ * lambda(omega) of Navarro, Bustos and Hitschfeld, "A Non-linear GPU Thread
+ * Map for Triangular Domains" (arXiv 1609.01490), with the bounding-box,
+ * rectangular-box, recursive-partition and upper-triangular maps of its
+ * Section 4.2 as comparison kernels.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named as device pointers must point to memory of the current
+ *    CUDA device; the caller owns all of it.  No entry point allocates device
+ *    memory.  Those that need scratch take a caller-provided `workspace` of at
+ *    least the size the matching *_workspace_size call reports.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every launch is asynchronous on it; results are ready when the
+ *    stream is synchronised.
+ *  - The return value is a tri_status.  It reports argument errors (checked
+ *    on the host before anything is launched) and launch errors.  Errors the
+ *    kernels detect on the device are written to device status words named in
+ *    the individual calls.
+ *  - Packed triangles are row-major lower triangles with the diagonal:
+ *    element (i, j), 0 <= j <= i < n, lives at offset i(i+1)/2 + j
+ *    (Eq. eq_matrix_indexing of Section 3.1 applied to elements), 64-bit.
+ *  - rho is the number of threads per block side (Section 3.1: blocks of
+ *    rho x rho threads); accepted values are 8, 16 and 32.
+ */
+#ifndef TRI_H
+#define TRI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TRI_API __attribute__((visibility("default")))
+#else
+#define TRI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TRI_OK = 0,
+    TRI_EINVAL = 1,    /* null pointer, unsupported rho/tile/enum value, zero size */
+    TRI_ERANGE = 2,    /* domain too large for the map (e.g. more than 2^32 blocks),
+                          or a size the map cannot cover (REC with a block count that
+                          is not a power of two) */
+    TRI_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    TRI_EOVERFLOW = 4, /* a bounded device list overflowed (reported through the
+                          device status of the call) */
+    TRI_ETIMEOUT = 5,  /* a bounded device wait gave up */
+    TRI_ENOSPACE = 6   /* workspace smaller than the size query reports */
+} tri_status;
+
+/* Block-space and thread-space maps (Sections 3 and 4.2). */
+typedef enum {
+    TRI_MAP_LAMBDA = 0,        /* lambda(omega), Eq. eq_gmap, 1-D (or 2-D beyond
+                                  2^31 - 1 blocks) grid of exactly m(m+1)/2 blocks */
+    TRI_MAP_BB = 1,            /* bounding box: m x m blocks, blocks above the
+                                  diagonal discarded (Section 4.2) */
+    TRI_MAP_RB = 2,            /* rectangular box: upper part folded under the
+                                  diagonal, ceil((m+1)/2) x m blocks (Section 4.2) */
+    TRI_MAP_REC = 3,           /* recursive partition: one diagonal pass plus one
+                                  launch per level; m must be a power of two */
+    TRI_MAP_UTM = 4,           /* upper-triangular map of Avril et al., thread space
+                                  (Section 4.2) */
+    TRI_MAP_LAMBDA_PDELTA = 5  /* lambda(omega) on the balanced m' x m' grid P_Delta,
+                                  m' = ceil(sqrt(m(m+1)/2)) (Section 3.1) */
+} tri_map;
+
+/* Square-root estimate inside lambda (Section 4.1).  Every variant is followed
+ * by an exact integer correction, so all three give identical maps. */
+typedef enum {
+    TRI_SQRT_X = 0, /* sqrtf(x)                                   (lambda_X) */
+    TRI_SQRT_R = 1, /* x * rsqrtf(x)                              (lambda_R) */
+    TRI_SQRT_N = 2  /* x * y, y = 1/sqrt(x) by three Newton steps from the
+                       0x5f3759df seed (Lomont)                   (lambda_N) */
+} tri_sqrt;
+
+typedef enum {
+    TRI_FP32 = 0,   /* direct differences in FP32 on CUDA cores */
+    TRI_BF16X3 = 1, /* Gram form on tcgen05 tensor cores: hi/lo BF16 split,
+                       3 products, FP32 accumulation, FP64 recompute of flagged pairs */
+    TRI_BF16X6 = 2  /* Gram form on tcgen05: hi/mid/lo BF16 split, 6 products,
+                       FP32 accumulation, FP64 recompute of flagged pairs */
+} tri_prec;
+
+typedef enum {
+    TRI_BODY_DUMMY = 0,    /* every mapped thread stores i+j to out[0] (Section 4.1's
+                              dummy kernel) */
+    TRI_BODY_SENTINEL = 1, /* stores only if i+j == 0xFFFFFFFF (never), so the time
+                              is the map alone */
+    TRI_BODY_COUNT = 2     /* atomically increments out[index(i,j)]: a coverage test */
+} tri_body;
+
+/* Human-readable name of a tri_status value (static storage). */
+TRI_API const char *tri_status_string(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+TRI_API int tri_version(void);
+
+/*
+ * tri_map_launch -- run one map over the element domain of size n.
+ *   Section 3.1 (lambda, Eq. eq_gmap / eq_theorem_nodiag), Section 4.1 (dummy
+ *   kernel, square-root variants), Section 4.2 (BB, RB, REC, UTM).
+ *   with_diag = 1: domain {0 <= j <= i < n}; with_diag = 0: {0 <= j < i < n}
+ *   (lambda then uses the strict form, Eq. eq_theorem_nodiag).
+ *   out (device, uint32): DUMMY/SENTINEL one word; COUNT n(n+1)/2 (with_diag)
+ *   or n(n-1)/2 counters, index i(i+1)/2 + j or i(i-1)/2 + j; the caller zeroes
+ *   them first.  sqrt_kind is used by the lambda maps only.
+ *   Errors: TRI_EINVAL (null out, bad enum, rho not 8/16/32, n = 0),
+ *   TRI_ERANGE (more than 2^32 - 1 blocks or threads; REC with ceil(n/rho) not
+ *   a power of two), TRI_ECUDA.
+ */
+TRI_API int tri_map_launch(int map, int sqrt_kind, uint32_t n, uint32_t rho, int with_diag,
+                   int body, uint32_t *out, void *stream);
+
+/*
+ * tri_lambda_verify -- evaluate lambda (Eq. eq_gmap, or Eq. eq_theorem_nodiag
+ * when with_diag = 0) for every omega in [w_begin, w_end), w_end <= 2^32,
+ * one thread per omega, and check each result against the exact row
+ * invariant T(i) <= omega < T(i+1), 0 <= j <= i (strict form: T(i-1) <= omega
+ * < T(i), 0 <= j < i), with T(i) = i(i+1)/2 in 64-bit integers.
+ *   result (device, 6 x uint64, zeroed by the caller) accumulates, modulo
+ *   2^64: [0] violations, [1] sum i, [2] sum j, [3] sum i*i, [4] sum j*j,
+ *   [5] sum i*j.
+ *   Errors: TRI_EINVAL, TRI_ERANGE (w_end > 2^32 or w_begin > w_end), TRI_ECUDA.
+ */
+TRI_API int tri_lambda_verify(int sqrt_kind, int with_diag, uint64_t w_begin, uint64_t w_end,
+                      unsigned long long *result, void *stream);
+
+/*
+ * tri_edm -- Euclidean distance matrix over i >= j (Section 5, test 2):
+ *   out[i(i+1)/2 + j] = sqrt(sum_k (x[i][k] - x[j][k])^2), the diagonal 0.
+ *   x (device, FP32) row-major [n][d]; out (device, FP32) n(n+1)/2 entries.
+ *   prec = TRI_FP32: blocks of rho x rho threads, each thread reg x reg pairs
+ *   (reg in {1, 2, 4}; 0 picks 1 for d <= 8, else 4); each block covers an
+ *   S x S pair tile, S = rho*reg, placed by `map` (any tri_map).  No workspace.
+ *   prec = TRI_BF16X3 / TRI_BF16X6: 128 x 128 pair tiles on tcgen05 tensor
+ *   cores, placed by TRI_MAP_LAMBDA or TRI_MAP_BB; rho and reg are ignored;
+ *   needs `workspace` of tri_edm_workspace_size bytes (16-byte aligned).
+ *   Pairs whose Gram estimate of d^2 falls below tau*(|x_i|^2 + |x_j|^2) are
+ *   recomputed in FP64 by direct differences; n_flagged (device uint64,
+ *   may be NULL) receives how many were flagged.  If more were flagged than
+ *   the workspace list holds, the recompute pass scans the whole triangle
+ *   instead (slower, same result).
+ *   Errors: TRI_EINVAL (null pointers, d = 0, bad enum/rho/reg, n = 0),
+ *   TRI_ERANGE (too many blocks for the map), TRI_ENOSPACE, TRI_ECUDA.
+ */
+TRI_API int tri_edm(const float *x, uint32_t n, uint32_t d, float *out, int map, uint32_t rho,
+            uint32_t reg, int prec, void *workspace, size_t ws_bytes,
+            unsigned long long *n_flagged, void *stream);
+
+/* Workspace bytes tri_edm needs for (n, d, prec); 0 for TRI_FP32. */
+TRI_API int tri_edm_workspace_size(uint32_t n, uint32_t d, int prec, size_t *bytes);
+
+/*
+ * tri_edm_batched -- many EDM triangles of uneven size in one persistent
+ * launch (lambda applied to each instance's own block numbers, found from
+ * an exclusive prefix sum of the per-instance block counts m_k(m_k+1)/2).
+ *   x_cat (device FP32): the instances' points, row-major, concatenated;
+ *   pt_off (device uint64 [count]): first row of instance k in x_cat;
+ *   n_k (device uint32 [count]): points in instance k (0 allowed);
+ *   out_cat (device FP32) / out_off (device uint64 [count]): instance k's
+ *   packed triangle starts at out_cat + out_off[k].
+ *   rho in {8,16,32}, reg in {1,2,4} as in tri_edm (FP32 direct differences).
+ *   workspace: tri_edm_batched_workspace_size bytes.  Issues two kernels and
+ *   no host synchronisation, so it can be captured in a CUDA graph.
+ *   Errors: TRI_EINVAL, TRI_ENOSPACE, TRI_ECUDA; an instance whose block count
+ *   overflows 32 bits sets device status word ws[0] to TRI_ERANGE and is skipped.
+ */
+TRI_API int tri_edm_batched(const float *x_cat, const uint64_t *pt_off, const uint32_t *n_k,
+                    uint32_t count, uint32_t d, float *out_cat, const uint64_t *out_off,
+                    uint32_t rho, uint32_t reg, void *workspace, size_t ws_bytes,
+                    void *stream);
+TRI_API int tri_edm_batched_workspace_size(uint32_t count, size_t *bytes);
+
+/*
+ * tri_ca_step -- one synchronous step of an outer-totalistic cellular
+ * automaton (Game of Life: birth_mask = 1<<3, survive_mask = 1<<2 | 1<<3) on
+ * the triangular domain {0 <= j <= i < n} (Section 1 lists cellular automata
+ * on triangular domains among the TD problems; Section 5 motivates the
+ * shared-memory tiled form).  A cell is alive when its byte is non-zero;
+ * neighbours outside the domain count as dead.  Each block stages a halo
+ * tile in shared memory; only domain cells of `out` are written (0 or 1).
+ *   in, out (device uint8) row-major with leading dimension ld (bytes);
+ *   ld >= n and ld a multiple of 16; in != out (no aliasing).
+ *   map: LAMBDA, LAMBDA_PDELTA, BB, RB or REC.  rho in {8,16,32}: a block of
+ *   rho x rho threads covers a (4 rho) x (4 rho) cell tile, each thread four
+ *   4-cell words.
+ *   Errors: TRI_EINVAL (null, aliasing, bad ld/rho/map), TRI_ERANGE, TRI_ECUDA.
+ */
+TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
+                uint32_t birth_mask, uint32_t survive_mask, int map, uint32_t rho,
+                void *stream);
+
+/*
+ * tet_map -- map blocks onto the discrete tetrahedron (Section 6): block
+ * omega -> (layer, row, col), layer >= row >= col, with the layer taken from
+ * the real root of x^3 + 3x^2 + 2x - 6 omega = 0 (an FP32 estimate plus an
+ * exact integer correction against T_k = k(k+1)(k+2)/6) and (row, col) from
+ * the 2-D lambda of omega - T_layer.  Blocks hold rho x rho threads, each
+ * looping over the rho elements of the third block index; the element
+ * domain is the strict triplets n > i > j > k >= 0.
+ *   out as in tri_map_launch; COUNT index C(i,3) + C(j,2) + k, C(n,3) counters.
+ *   Errors: TRI_EINVAL, TRI_ERANGE (more than 2^32 - 1 blocks), TRI_ECUDA.
+ */
+TRI_API int tet_map(uint32_t n, uint32_t rho, int body, uint32_t *out, void *stream);
+
+/*
+ * tet_at_energy -- Axilrod-Teller triple-dipole energy of n points, a
+ * triplet-interaction n-body sum over the tetrahedral domain (Section 6):
+ *   E = sum_{i>j>k} nu (1 + 3 cos g_i cos g_j cos g_k) / (r_ij r_jk r_ki)^3.
+ *   xyz (device FP32 [n][3]); energy (device, one double).  Terms in FP32,
+ *   block partials in FP64 written to the workspace, then summed in a fixed
+ *   order by a second kernel, so the result is deterministic.
+ *   map: TRI_MAP_LAMBDA (tetrahedral lambda) or TRI_MAP_BB (m^3 box with
+ *   discard).  rho in {8,16,32}.
+ *   Errors: TRI_EINVAL, TRI_ERANGE, TRI_ENOSPACE, TRI_ECUDA.
+ */
+TRI_API int tet_at_energy(const float *xyz, uint32_t n, double nu, double *energy, int map,
+                  uint32_t rho, void *workspace, size_t ws_bytes, void *stream);
+TRI_API int tet_at_workspace_size(uint32_t n, uint32_t rho, int map, size_t *bytes);
+
+/*
+ * MLP cost model y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 (one output), used
+ * to predict the log run time of a (kernel, n, d, map, rho) configuration.
+ * Not in the paper.  theta (device FP32) holds W1 [H1][F], b1 [H1],
+ * W2 [H2][H1], b2 [H2], W3 [H2], b3 [1] contiguously, row-major.
+ * X (device FP32 [B][F]), y (device FP32 [B]).  H1, H2 <= 128, F <= 64.
+ * workspace: tri_mlp_workspace_size bytes (activations of the batch).
+ *
+ *   tri_mlp_forward: pred[b] for every row of X.
+ *   tri_mlp_grad:    loss = mean_b (pred[b] - y[b])^2 into *loss (device float)
+ *                    and its gradient w.r.t. theta into grad (device, overwritten).
+ *   tri_mlp_adam:    one Adam step (t counts from 1) on theta with moments m, v.
+ *   tri_mlp_argmin:  forward over B candidate rows and write the index of the
+ *                    smallest prediction to *best (device uint32).
+ */
+TRI_API int tri_mlp_workspace_size(uint32_t B, uint32_t H1, uint32_t H2, size_t *bytes);
+TRI_API int tri_mlp_forward(const float *theta, const float *X, uint32_t B, uint32_t F, uint32_t H1,
+                    uint32_t H2, float *pred, void *workspace, size_t ws_bytes, void *stream);
+TRI_API int tri_mlp_grad(const float *theta, const float *X, const float *y, uint32_t B, uint32_t F,
+                 uint32_t H1, uint32_t H2, float *loss, float *grad, void *workspace,
+                 size_t ws_bytes, void *stream);
+TRI_API int tri_mlp_adam(float *theta, const float *grad, float *m, float *v, uint32_t nparams,
+                 uint32_t t, float lr, float beta1, float beta2, float eps, void *stream);
+TRI_API int tri_mlp_argmin(const float *theta, const float *X, uint32_t B, uint32_t F, uint32_t H1,
+                   uint32_t H2, uint32_t *best, void *workspace, size_t ws_bytes,
+                   void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRI_H */

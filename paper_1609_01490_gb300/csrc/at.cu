@@ -1,0 +1,136 @@
+// Axilrod-Teller triple-dipole energy over the strict triplets i > j > k:
+// a triplet-interaction n-body sum on the tetrahedral domain of Section 6,
+// with blocks placed by the tetrahedral lambda or by an m^3 bounding box.
+#include <cuda_runtime.h>
+
+#include "tri_maps.cuh"
+
+using namespace tri;
+
+namespace {
+
+// Block (L, R, C), L >= R >= C, of rho x rho threads: thread (ty, tx) takes
+// i = L*rho + ty and j = R*rho + tx and loops k over block C (k < j).  With
+// squared sides a = |ij|^2, b = |jk|^2, c = |ki|^2 the law of cosines gives
+// cos g_i cos g_j cos g_k = (a+c-b)(a+b-c)(b+c-a) / (8abc) and
+// (r_ij r_jk r_ki)^3 = (abc)^(3/2).  Terms are formed and summed per thread in
+// FP32, then reduced over the block in FP64 into partial[T3(L)+T2(R)+C].
+template <int MAP>
+__global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, uint32_t m, uint64_t nblocks,
+                          double *__restrict__ partial)
+{
+    uint32_t L, R, C;
+    if constexpr (MAP == MAP_LAMBDA) {
+        const uint64_t w = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        if (w >= nblocks) return;
+        tet_block((uint32_t)w, L, R, C);
+    } else {
+        C = blockIdx.x;
+        R = blockIdx.y;
+        L = blockIdx.z;
+        if (R > L || C > R) return;
+    }
+    __shared__ float pk[32][3];
+    __shared__ double wsum[32];
+    const uint32_t rho = blockDim.x;
+    const uint32_t tid = threadIdx.y * rho + threadIdx.x;
+    if (tid < rho) {
+        const uint32_t k = C * rho + tid;
+        pk[tid][0] = k < n ? p[3 * k + 0] : 0.0f;
+        pk[tid][1] = k < n ? p[3 * k + 1] : 0.0f;
+        pk[tid][2] = k < n ? p[3 * k + 2] : 0.0f;
+    }
+    __syncthreads();
+    const uint32_t i = L * rho + threadIdx.y, j = R * rho + threadIdx.x;
+    float s = 0.0f;
+    if (i < n && j < i) {
+        const float xi = p[3 * i], yi = p[3 * i + 1], zi = p[3 * i + 2];
+        const float xj = p[3 * j], yj = p[3 * j + 1], zj = p[3 * j + 2];
+        const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
+        const float a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const uint32_t kend = min(j, (C + 1) * rho) - C * rho;  // k < j
+        for (uint32_t t = 0; t < kend; ++t) {
+            const float ex = xj - pk[t][0], ey = yj - pk[t][1], ez = zj - pk[t][2];
+            const float fx = pk[t][0] - xi, fy = pk[t][1] - yi, fz = pk[t][2] - zi;
+            const float b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            const float c = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+            const float q = a * b * c;
+            const float P = (a + c - b) * (a + b - c) * (b + c - a);
+            const float rs = rsqrtf(q);
+            const float inv = rs * rs;
+            s += fmaf(0.375f * P, inv, 1.0f) * inv * rs;
+        }
+    }
+    double v = nu * (double)s;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const uint32_t nthreads = rho * rho, lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (uint32_t q = 0; q < (nthreads + 31) / 32; ++q) t += wsum[q];
+        partial[T3(L) + T2(R) + C] = t;
+    }
+}
+
+// Fixed-order sum of the partials: thread t adds a contiguous run, then
+// thread 0 adds the run totals in order.
+__global__ void at_reduce_kernel(const double *__restrict__ partial, uint64_t count, double *__restrict__ energy)
+{
+    __shared__ double part[1024];
+    const uint32_t t = threadIdx.x, nt = blockDim.x;
+    const uint64_t per = (count + nt - 1) / nt;
+    const uint64_t b0 = min(count, (uint64_t)t * per), b1 = min(count, b0 + per);
+    double s = 0.0;
+    for (uint64_t q = b0; q < b1; ++q) s += partial[q];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        double e = 0.0;
+        for (uint32_t q = 0; q < nt; ++q) e += part[q];
+        *energy = e;
+    }
+}
+
+}  // namespace
+
+extern "C" int tet_at_workspace_size(uint32_t n, uint32_t rho, int map, size_t *bytes)
+{
+    if (!bytes || !trihost::rho_ok(rho)) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    const uint64_t m = ((uint64_t)n + rho - 1) / rho;
+    *bytes = (size_t)(T3(m) * sizeof(double));
+    return TRI_OK;
+}
+
+// Launches the partial-sum kernel into `partial` (at least T3(m) doubles) and
+// the fixed-order reduction into *energy.
+static int at_energy_launch(const float *xyz, uint32_t n, double nu, double *energy, int map, uint32_t rho,
+                      double *partial, cudaStream_t s)
+{
+    const uint64_t m = ((uint64_t)n + rho - 1) / rho;
+    const uint64_t nb = T3(m);
+    const dim3 blk(rho, rho);
+    if (map == TRI_MAP_LAMBDA) {
+        if (nb > 0xFFFFFFFFull) return TRI_ERANGE;
+        at_kernel<MAP_LAMBDA><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, nb, partial);
+    } else {
+        if (m > 65535) return TRI_ERANGE;
+        at_kernel<MAP_BB><<<dim3((unsigned)m, (unsigned)m, (unsigned)m), blk, 0, s>>>(xyz, n, nu, (uint32_t)m,
+                                                                                        nb, partial);
+    }
+    if (cudaGetLastError() != cudaSuccess) return TRI_ECUDA;
+    at_reduce_kernel<<<1, 1024, 0, s>>>(partial, nb, energy);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+extern "C" int tet_at_energy(const float *xyz, uint32_t n, double nu, double *energy, int map, uint32_t rho,
+                             void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!xyz || !energy || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    size_t need = 0;
+    tet_at_workspace_size(n, rho, map, &need);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 7)) return TRI_ENOSPACE;
+    return at_energy_launch(xyz, n, nu, energy, map, rho, (double *)workspace, (cudaStream_t)stream);
+}

@@ -1,0 +1,308 @@
+// Euclidean distance matrix on CUDA cores in FP32 by direct differences
+// (Section 5, test 2), single triangles under any map, and many uneven
+// triangles in one persistent launch.
+#include <cuda_runtime.h>
+
+#include "tri_internal.h"
+#include "tri_maps.cuh"
+
+using namespace tri;
+
+namespace {
+
+constexpr int KC = 32;  // features staged per shared-memory pass
+
+// One S x S pair tile, S = RHO*R, of the triangle over points x[0..n) (row-major,
+// d features): rows i0 = bi*S.., columns j0 = bj*S...  Thread (ty, tx) owns
+// rows ty + u*RHO and columns tx + v*RHO (u, v < R), so a warp's stores for
+// fixed (u, v) fall on consecutive columns of one or two rows.
+template <int RHO, int R>
+__device__ __forceinline__ void edm_tile(const float *__restrict__ x, uint32_t n, uint32_t d,
+                                         float *__restrict__ out, uint32_t bi, uint32_t bj,
+                                         float (*si)[RHO * R + 1], float (*sj)[RHO * R + 1])
+{
+    constexpr int S = RHO * R;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RHO + tx;
+    const uint64_t i0 = (uint64_t)bi * S, j0 = (uint64_t)bj * S;
+    float acc[R][R];
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+#pragma unroll
+        for (int v = 0; v < R; ++v) acc[u][v] = 0.0f;
+
+    for (uint32_t k0 = 0; k0 < d; k0 += KC) {
+        const uint32_t kc = min((uint32_t)KC, d - k0);
+        // stage x[i0 + r][k0 + k] and x[j0 + r][k0 + k], transposed to [k][r]
+        for (uint32_t t = tid; t < (uint32_t)S * kc; t += RHO * RHO) {
+            const uint32_t r = t / kc, k = t - r * kc;
+            const uint64_t gi = i0 + r, gj = j0 + r;
+            si[k][r] = gi < n ? x[gi * d + k0 + k] : 0.0f;
+            sj[k][r] = gj < n ? x[gj * d + k0 + k] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (uint32_t k = 0; k < kc; ++k) {
+            float a[R], b[R];
+#pragma unroll
+            for (int u = 0; u < R; ++u) a[u] = si[k][ty + u * RHO];
+#pragma unroll
+            for (int v = 0; v < R; ++v) b[v] = sj[k][tx + v * RHO];
+#pragma unroll
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int v = 0; v < R; ++v) {
+                    const float df = a[u] - b[v];
+                    acc[u][v] = fmaf(df, df, acc[u][v]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const uint64_t i = i0 + ty + u * RHO;
+        if (i >= n) continue;
+        float *row = out + T2(i);
+#pragma unroll
+        for (int v = 0; v < R; ++v) {
+            const uint64_t j = j0 + tx + v * RHO;
+            if (j <= i) row[j] = sqrtf(acc[u][v]);
+        }
+    }
+}
+
+template <int MAP, int RHO, int R>
+__global__ void __launch_bounds__(RHO *RHO) edm_kernel(const float *__restrict__ x, uint32_t n, uint32_t d,
+                                                       float *__restrict__ out, BlockMap bm)
+{
+    __shared__ float si[KC][RHO * R + 1];
+    __shared__ float sj[KC][RHO * R + 1];
+    uint32_t bi, bj;
+    if (!map_block<MAP>(bm, bi, bj)) return;
+    edm_tile<RHO, R>(x, n, d, out, bi, bj, si, sj);
+}
+
+// UTM is a thread-space map: one thread per pair, no tile to stage.
+__global__ void edm_utm_kernel(const float *__restrict__ x, uint32_t n, uint32_t d, float *__restrict__ out)
+{
+    const uint64_t N = (uint64_t)n + 1;
+    const uint64_t total = N * n / 2;
+    const uint64_t k = ((uint64_t)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y) +
+                       threadIdx.y * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    uint32_t a, b;
+    utm_pair(k, N, a, b);
+    const uint64_t i = b - 2, j = a - 1;
+    const float *xi = x + i * d, *xj = x + j * d;
+    float acc = 0.0f;
+    for (uint32_t t = 0; t < d; ++t) {
+        const float df = xi[t] - xj[t];
+        acc = fmaf(df, df, acc);
+    }
+    out[T2(i) + j] = sqrtf(acc);
+}
+
+template <int MAP, int RHO, int R>
+cudaError_t launch_one(dim3 g, cudaStream_t s, const float *x, uint32_t n, uint32_t d, float *out, BlockMap bm)
+{
+    edm_kernel<MAP, RHO, R><<<g, dim3(RHO, RHO), 0, s>>>(x, n, d, out, bm);
+    return cudaGetLastError();
+}
+
+template <int MAP>
+cudaError_t launch_rr(uint32_t rho, uint32_t reg, dim3 g, cudaStream_t s, const float *x, uint32_t n, uint32_t d,
+                      float *out, BlockMap bm)
+{
+#define TRI_E(RH, RG)                                                                                          \
+    if (rho == RH && reg == RG) return launch_one<MAP, RH, RG>(g, s, x, n, d, out, bm);
+    TRI_E(8, 1) TRI_E(8, 2) TRI_E(8, 4) TRI_E(16, 1) TRI_E(16, 2) TRI_E(16, 4) TRI_E(32, 1) TRI_E(32, 2)
+    TRI_E(32, 4)
+#undef TRI_E
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ batched ----
+// Exclusive prefix sum of the per-instance block counts m_k(m_k+1)/2 into
+// off[0..count], in one block with a fixed order (no inter-block waiting).
+__global__ void batched_scan_kernel(const uint32_t *__restrict__ n_k, uint32_t count, uint32_t S,
+                                    uint64_t *__restrict__ off, int *__restrict__ status)
+{
+    __shared__ uint64_t part[1024];
+    const uint32_t t = threadIdx.x, nt = blockDim.x;
+    const uint32_t per = (count + nt - 1) / nt;
+    const uint32_t b0 = min(count, t * per), b1 = min(count, b0 + per);
+    uint64_t s = 0;
+    for (uint32_t k = b0; k < b1; ++k) {
+        const uint64_t m = (n_k[k] + (uint64_t)S - 1) / S;
+        const uint64_t nb = T2(m);
+        if (nb <= 0xFFFFFFFFull) s += nb;
+    }
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        uint64_t run = 0;
+        for (uint32_t q = 0; q < nt; ++q) {
+            const uint64_t v = part[q];
+            part[q] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    uint64_t run = part[t];
+    for (uint32_t k = b0; k < b1; ++k) {
+        off[k] = run;
+        const uint64_t m = (n_k[k] + (uint64_t)S - 1) / S;
+        const uint64_t nb = T2(m);
+        if (nb <= 0xFFFFFFFFull) {
+            run += nb;
+        } else {
+            atomicExch(status, (int)TRI_ERANGE);  // instance skipped: lambda needs omega < 2^32
+        }
+    }
+    if (t == nt - 1) off[count] = run;
+}
+
+// Persistent CTAs walk the global block numbers omega_g with a grid stride;
+// each finds its instance by binary search over the block offsets (staged in
+// shared memory when they fit) and maps the local number with lambda.
+template <int RHO, int R>
+__global__ void __launch_bounds__(RHO *RHO)
+    edm_batched_kernel(const float *__restrict__ x_cat, const uint64_t *__restrict__ pt_off,
+                       const uint32_t *__restrict__ n_k, uint32_t count, uint32_t d, float *__restrict__ out_cat,
+                       const uint64_t *__restrict__ out_off, const uint64_t *__restrict__ boff, uint32_t smem_cnt)
+{
+    __shared__ float si[KC][RHO * R + 1];
+    __shared__ float sj[KC][RHO * R + 1];
+    extern __shared__ uint64_t soff[];
+    const bool in_smem = smem_cnt >= count + 1;
+    if (in_smem)
+        for (uint32_t t = threadIdx.y * RHO + threadIdx.x; t <= count; t += RHO * RHO) soff[t] = boff[t];
+    __syncthreads();
+    const uint64_t *off = in_smem ? soff : boff;
+    const uint64_t total = off[count];
+    for (uint64_t wg = blockIdx.x; wg < total; wg += gridDim.x) {
+        // largest k with off[k] <= wg (instances with no blocks are skipped)
+        uint32_t lo = 0, hi = count;  // off[lo] <= wg < off[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= wg) lo = mid;
+            else hi = mid;
+        }
+        uint32_t bi, bj;
+        lambda_diag<TRI_SQRT_R>((uint32_t)(wg - off[lo]), bi, bj);
+        edm_tile<RHO, R>(x_cat + pt_off[lo] * d, n_k[lo], d, out_cat + out_off[lo], bi, bj, si, sj);
+    }
+}
+
+template <int RHO, int R>
+cudaError_t launch_batched_one(cudaStream_t s, const float *x_cat, const uint64_t *pt_off, const uint32_t *n_k,
+                               uint32_t count, uint32_t d, float *out_cat, const uint64_t *out_off,
+                               const uint64_t *boff)
+{
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t smem_cnt = count + 1;
+    if (smem_cnt > 4096) smem_cnt = 0;  // large batches search the offsets in global memory
+    const size_t dyn = (size_t)smem_cnt * sizeof(uint64_t);
+    if (cudaFuncSetAttribute(edm_batched_kernel<RHO, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+        cudaSuccess)
+        return cudaErrorInvalidValue;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, edm_batched_kernel<RHO, R>, RHO * RHO, dyn);
+    if (per < 1) per = 1;
+    edm_batched_kernel<RHO, R><<<nsm * per, dim3(RHO, RHO), dyn, s>>>(x_cat, pt_off, n_k, count, d, out_cat,
+                                                                       out_off, boff, smem_cnt);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int trihost::edm_fp32(const float *x, uint32_t n, uint32_t d, float *out, int map, uint32_t rho, uint32_t reg,
+                      cudaStream_t s)
+{
+    if (reg == 0) reg = d <= 8 ? 1 : 4;
+    if (reg != 1 && reg != 2 && reg != 4) return TRI_EINVAL;
+    if (map == TRI_MAP_UTM) {
+        const uint64_t N = (uint64_t)n + 1, total = N * n / 2, tpb = (uint64_t)rho * rho;
+        if (total > 0xFFFFFFFFull) return TRI_ERANGE;
+        edm_utm_kernel<<<trihost::linear_grid((total + tpb - 1) / tpb), dim3(rho, rho), 0, s>>>(x, n, d, out);
+        return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+    }
+    const uint32_t S = rho * reg;
+    const uint32_t m = (n + S - 1) / S;
+    BlockMap bm{};
+    bm.m = m;
+    bm.nblocks = T2(m);
+    cudaError_t e = cudaSuccess;
+    switch (map) {
+    case TRI_MAP_LAMBDA:
+        if (bm.nblocks > 0xFFFFFFFFull) return TRI_ERANGE;
+        e = launch_rr<MAP_LAMBDA>(rho, reg, trihost::linear_grid(bm.nblocks), s, x, n, d, out, bm);
+        break;
+    case TRI_MAP_LAMBDA_PDELTA: {
+        if (bm.nblocks > 0xFFFFFFFFull) return TRI_ERANGE;
+        const uint64_t mp = trihost::isqrt_ceil(bm.nblocks);
+        if (mp > 65535) return TRI_ERANGE;
+        e = launch_rr<MAP_LAMBDA_PD>(rho, reg, dim3((unsigned)mp, (unsigned)mp), s, x, n, d, out, bm);
+        break;
+    }
+    case TRI_MAP_BB:
+        if (m > 65535) return TRI_ERANGE;
+        e = launch_rr<MAP_BB>(rho, reg, dim3(m, m), s, x, n, d, out, bm);
+        break;
+    case TRI_MAP_RB: {
+        const uint32_t h = (m & 1u) ? (m + 1) / 2 : m / 2 + 1;
+        if (h > 65535) return TRI_ERANGE;
+        e = launch_rr<MAP_RB>(rho, reg, dim3(m, h), s, x, n, d, out, bm);
+        break;
+    }
+    case TRI_MAP_REC: {
+        if (!trihost::is_pow2(m)) return TRI_ERANGE;
+        const uint32_t k = trihost::ilog2(m);
+        if (k > 0 && m / 2 > 65535) return TRI_ERANGE;
+        for (uint32_t l = 0; l <= k && e == cudaSuccess; ++l) {
+            bm.level = l;
+            const dim3 g = l == 0 ? dim3(m) : dim3(1u << (l - 1), m / 2);
+            e = launch_rr<MAP_REC>(rho, reg, g, s, x, n, d, out, bm);
+        }
+        break;
+    }
+    default:
+        return TRI_EINVAL;
+    }
+    return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+extern "C" int tri_edm_batched_workspace_size(uint32_t count, size_t *bytes)
+{
+    if (!bytes) return TRI_EINVAL;
+    *bytes = 16 + sizeof(uint64_t) * ((size_t)count + 1);
+    return TRI_OK;
+}
+
+extern "C" int tri_edm_batched(const float *x_cat, const uint64_t *pt_off, const uint32_t *n_k, uint32_t count,
+                               uint32_t d, float *out_cat, const uint64_t *out_off, uint32_t rho, uint32_t reg,
+                               void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!x_cat || !pt_off || !n_k || !out_cat || !out_off || !workspace || d == 0 || count == 0)
+        return TRI_EINVAL;
+    if (!trihost::rho_ok(rho)) return TRI_EINVAL;
+    if (reg == 0) reg = d <= 8 ? 1 : 4;
+    if (reg != 1 && reg != 2 && reg != 4) return TRI_EINVAL;
+    size_t need = 0;
+    tri_edm_batched_workspace_size(count, &need);
+    if (ws_bytes < need || ((uintptr_t)workspace & 15)) return TRI_ENOSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *status = (int *)workspace;
+    uint64_t *boff = (uint64_t *)((char *)workspace + 16);
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return TRI_ECUDA;
+    batched_scan_kernel<<<1, 1024, 0, s>>>(n_k, count, rho * reg, boff, status);
+    if (cudaGetLastError() != cudaSuccess) return TRI_ECUDA;
+    cudaError_t e = cudaErrorInvalidValue;
+#define TRI_B(RH, RG)                                                                                          \
+    if (rho == RH && reg == RG)                                                                                \
+        e = launch_batched_one<RH, RG>(s, x_cat, pt_off, n_k, count, d, out_cat, out_off, boff);
+    TRI_B(8, 1) TRI_B(8, 2) TRI_B(8, 4) TRI_B(16, 1) TRI_B(16, 2) TRI_B(16, 4) TRI_B(32, 1) TRI_B(32, 2)
+    TRI_B(32, 4)
+#undef TRI_B
+    return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}

@@ -1,0 +1,682 @@
+// Euclidean distance matrix on tcgen05 tensor cores (not in the paper, which
+// evaluates distances directly): d_ij^2 = |x_i|^2 + |x_j|^2 - 2 x_i.x_j with the
+// Gram term x_i.x_j from BF16 products accumulated in FP32 in tensor memory.
+//
+// Precision.  Each FP32 input is split into BF16 planes, x = hi + lo (+ mid):
+//   hi = bf16(x), r = x - hi (exact), mid = bf16(r), lo = bf16(r - mid).
+// Three planes represent x exactly (3 x 8 significant bits = FP32's 24);
+// the Gram term keeps the products hi.hi', hi.mid', mid.hi', hi.lo', lo.hi',
+// mid.mid' (BF16X6) and drops those below 2^-24 |x||y|; the two-plane form
+// (BF16X3) keeps hi.hi', hi.lo', lo.hi'.  Every BF16 x BF16 product is exact
+// in FP32.  A pair whose estimate falls below tau (|x_i|^2 + |x_j|^2) has lost
+// too many digits to cancellation and is flagged; a second kernel recomputes
+// flagged pairs in FP64 by direct differences (the paper's definition).
+//
+// Kernels.  prepare: FP64 row norms (stored as FP32) and the BF16 planes,
+// K padded to a multiple of 64.  gram: persistent, one CTA per SM, 128 x 128
+// pair tiles taken in lambda order (Eq. eq_gmap) as one contiguous run of
+// tile numbers per CTA, so consecutive tiles share their row block and the
+// CTA keeps that row block's planes (A) resident in shared memory while TMA
+// streams the column blocks (B) through a ring of stages.  Warp 0 issues TMA,
+// warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator, warps
+// 2-5 read TMEM back, form the distances, flag cancellations and store the
+// packed rows.  fixup: FP64 recompute of the flagged pairs.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "tri_internal.h"
+#include "tri_maps.cuh"
+
+using namespace tri;
+
+namespace {
+
+constexpr int TILE = 128;                  // pair tile side (UMMA M = N = 128)
+constexpr int KCH = 64;                    // K per chunk: one 128-byte swizzle row of BF16
+constexpr int CHUNK_BYTES = TILE * KCH * 2;  // 16 KB: 128 rows x 64 BF16
+constexpr int NTHREADS = 192;              // 6 warps
+constexpr int EPI_STAGE_FLOATS = 32 * 33;  // per epilogue warp transposition buffer
+constexpr uint32_t SPIN_LIMIT = 1u << 24;  // bounded waits (with nanosleep: well over a second)
+constexpr int SMEM_LIMIT = 227 * 1024;
+
+constexpr float TAU_X6 = 0.3125f;  // flag threshold for hi/mid/lo (derived bound)
+constexpr float TAU_X3 = 0.0625f;  // flag threshold for hi/lo (empirical)
+
+struct WsLayout {
+    size_t hdr, norms, planes, flags, total;
+    unsigned long long cap;
+};
+
+// Workspace: [header 256 B: flag counter, status][norms n FP32][planes
+// P x n x dp BF16][flag list cap x u64], each part 256-byte aligned.
+WsLayout ws_layout(uint32_t n, uint32_t d, int prec)
+{
+    const int P = prec == TRI_BF16X6 ? 3 : 2;
+    const size_t dp = ((size_t)d + KCH - 1) / KCH * KCH;
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    WsLayout L;
+    L.hdr = 0;
+    L.norms = 256;
+    L.planes = al(L.norms + sizeof(float) * n);
+    L.cap = (unsigned long long)std::max<size_t>(1u << 20, 4 * (size_t)n);
+    L.flags = al(L.planes + (size_t)P * n * dp * 2);
+    L.total = al(L.flags + L.cap * sizeof(unsigned long long));
+    return L;
+}
+
+// --------------------------------------------------------------- PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete.  Gives up after
+// SPIN_LIMIT polls, or early when another role has already given up (unless
+// abort_flag is null: the drain waits at exit must not cut short a copy or
+// MMA that is still writing).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (abort_flag && *abort_flag) return false;
+            __nanosleep(128);
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
+                                            int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (start, leading and stride offsets in 16-byte units).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 128 (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16).
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                           ((uint32_t)(TILE >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// ------------------------------------------------------------ prepare ----
+// One warp per row: FP64 norm (rounded to FP32) and the BF16 planes.
+template <int P>
+__global__ void prepare_kernel(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t dp,
+                               float *__restrict__ norms, __nv_bfloat16 *__restrict__ planes)
+{
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const float *row = x + (size_t)warp * d;
+    double s = 0.0;
+    for (uint32_t k = lane; k < dp; k += 32) {
+        const float v = k < d ? row[k] : 0.0f;
+        s += (double)v * (double)v;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(hi);
+        const size_t o = (size_t)warp * dp + k;
+        planes[o] = hi;
+        if constexpr (P == 2) {
+            planes[(size_t)n * dp + o] = __float2bfloat16_rn(r1);
+        } else {
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(mid);
+            planes[(size_t)n * dp + o] = mid;
+            planes[2 * (size_t)n * dp + o] = __float2bfloat16_rn(r2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) norms[warp] = (float)s;
+}
+
+// --------------------------------------------------------------- gram ----
+struct GramArgs {
+    uint32_t n, nkc;           // points, 64-wide K chunks
+    uint32_t m;                // tile rows of the triangle
+    uint64_t ntiles;           // tile numbers walked: m(m+1)/2 (lambda) or m*m (BB)
+    uint32_t stages;           // B ring depth
+    float tau;
+    const float *norms;
+    float *out;
+    unsigned long long *flag_count, *flag_list, flag_cap;
+    int *status;
+};
+
+template <int MAP>
+__device__ __forceinline__ bool tile_of(uint64_t t, uint32_t m, uint32_t &bi, uint32_t &bj)
+{
+    if constexpr (MAP == MAP_LAMBDA) {
+        lambda_diag<TRI_SQRT_R>((uint32_t)t, bi, bj);
+        return true;
+    } else {
+        bi = (uint32_t)(t / m);
+        bj = (uint32_t)(t - (uint64_t)bi * m);
+        return bj <= bi;  // bounding box: tiles above the diagonal are skipped
+    }
+}
+
+// Products (A plane, B plane) kept by the split: P = 3 -> 6 products, P = 2 -> 3.
+__device__ __constant__ uint8_t kProdA[6] = {0, 0, 1, 0, 2, 1};
+__device__ __constant__ uint8_t kProdB[6] = {0, 1, 0, 2, 0, 1};
+
+template <int MAP, int P>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gram_kernel(const __grid_constant__ CUtensorMap tmap, const GramArgs g)
+{
+    constexpr int NPROD = P == 3 ? 6 : 3;
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte aligned operand area
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;
+    const uint32_t stage_bytes = (uint32_t)P * CHUNK_BYTES;
+    const uint32_t sA = base;                                  // [kc][p] chunks
+    const uint32_t sB = base + a_bytes;                        // [stage][p] chunks
+    float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(epi + 4 * EPI_STAGE_FLOATS);
+    // barriers: fullA, freeA, done, tmem_full[2], tmem_empty[2], fullB[stages], emptyB[stages]
+    const uint32_t bar0 = smem_u32(bars);
+    const uint32_t b_fullA = bar0, b_freeA = bar0 + 8, b_done = bar0 + 16;
+    const uint32_t b_tfull = bar0 + 24, b_tempty = bar0 + 40;
+    const uint32_t b_fullB = bar0 + 56, b_emptyB = bar0 + 56 + 8 * g.stages;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        mbar_init(b_fullA, 1);
+        mbar_init(b_freeA, 1);
+        mbar_init(b_done, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(b_tfull + 8 * i, 1);
+            mbar_init(b_tempty + 8 * i, 4);  // one arrival per epilogue warp
+        }
+        for (uint32_t s = 0; s < g.stages; ++s) {
+            mbar_init(b_fullB + 8 * s, 1);
+            mbar_init(b_emptyB + 8 * s, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // this CTA's contiguous run of tile numbers
+    const uint64_t per = (g.ntiles + gridDim.x - 1) / gridDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * per;
+    const uint64_t t1 = t0 + per < g.ntiles ? t0 + per : g.ntiles;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0;
+            uint32_t issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            bool ok = true;
+            for (uint64_t t = t0; t < t1 && ok; ++t) {
+                uint32_t bi, bj;
+                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+                if (bi != a_row) {
+                    if (a_loads > 0 && !mbar_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(b_fullA, a_bytes);
+                    for (uint32_t kc = 0; kc < g.nkc; ++kc)
+                        for (int p = 0; p < P; ++p)
+                            tma_load_3d(sA + (kc * P + p) * CHUNK_BYTES, &tmap, b_fullA, kc * KCH, bi * TILE, p);
+                    ++a_loads;
+                    a_row = bi;
+                }
+                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
+                    if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(b_fullB + 8 * stage, stage_bytes);
+                    for (int p = 0; p < P; ++p)
+                        tma_load_3d(sB + (stage * P + p) * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH,
+                                    bj * TILE, p);
+                    ++issued[stage];
+                    if (++stage == g.stages) {
+                        stage = 0;
+                        b_phase ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(g.status, (int)TRI_ETIMEOUT);
+            }
+            // never leave a copy in flight: wait for the last load of every stage
+            for (uint32_t s = 0; s < g.stages; ++s)
+                if (issued[s]) mbar_wait(b_fullB + 8 * s, (issued[s] - 1) & 1, nullptr);
+            if (a_loads) mbar_wait(b_fullA, (a_loads - 1) & 1, nullptr);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, acc = 0, acc_phase = 0;
+            bool ok = true, any = false;
+            for (uint64_t t = t0; t < t1 && ok; ++t) {
+                uint32_t bi, bj;
+                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+                if (bi != a_row) {
+                    if (a_loads > 0) umma_commit(b_freeA);  // old A is free once issued MMAs finish
+                    if (!mbar_wait(b_fullA, a_loads & 1, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    ++a_loads;
+                    a_row = bi;
+                }
+                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + acc * TILE;
+                uint32_t accumulate = 0;
+                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
+                    if (!mbar_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int q = 0; q < NPROD; ++q) {
+                        const uint32_t a_chunk = sA + (kc * P + kProdA[q]) * CHUNK_BYTES;
+                        const uint32_t b_chunk = sB + (stage * P + kProdB[q]) * CHUNK_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < KCH / 16; ++kk) {
+                            umma_bf16(d_tmem, sdesc(a_chunk + kk * 32), sdesc(b_chunk + kk * 32), accumulate);
+                            accumulate = 1;
+                        }
+                    }
+                    umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
+                    if (++stage == g.stages) {
+                        stage = 0;
+                        b_phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(b_tfull + 8 * acc);  // accumulator ready for the epilogue
+                any = true;
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1;
+                }
+            }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(g.status, (int)TRI_ETIMEOUT);
+            }
+            // all issued MMAs complete before TMEM is released
+            umma_commit(b_done);
+            mbar_wait(b_done, 0, nullptr);
+            (void)any;
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..5)
+        const uint32_t q = warp & 3;  // TMEM lane quarter this warp may access
+        float *stg = epi + (warp - 2) * EPI_STAGE_FLOATS;
+        uint32_t acc = 0, acc_phase = 0;
+        for (uint64_t t = t0; t < t1; ++t) {
+            uint32_t bi, bj;
+            if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+            int ready = 0;
+            if (lane == 0) ready = mbar_wait(b_tfull + 8 * acc, acc_phase, &s_abort) ? 1 : 0;
+            ready = __shfl_sync(0xffffffffu, ready, 0);  // warp-uniform, and the warp reconverges
+            if (!ready) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicExch(g.status, (int)TRI_ETIMEOUT);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t row0 = bi * TILE + q * 32;      // this warp's first row
+            const uint32_t i = row0 + lane;                 // this thread's row
+            const float ni = i < g.n ? __ldg(g.norms + i) : 0.0f;
+            for (int c = 0; c < TILE / 32; ++c) {
+                const uint32_t col0 = bj * TILE + c * 32;
+                float v[32];
+                tmem_ld32(tmem + ((q * 32) << 16) + acc * TILE + c * 32, v);
+                const uint32_t jl = col0 + lane;
+                const float nj_l = jl < g.n ? __ldg(g.norms + jl) : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const float nj = __shfl_sync(0xffffffffu, nj_l, k);
+                    const uint32_t j = col0 + k;
+                    const float s = ni + nj;
+                    const float d2 = fmaf(-2.0f, v[k], s);
+                    float dist = sqrtf(fmaxf(d2, 0.0f));
+                    if (i == j) dist = 0.0f;
+                    if (i < g.n && j < i && d2 < g.tau * s) {
+                        const unsigned long long slot = atomicAdd(g.flag_count, 1ull);
+                        if (slot < g.flag_cap) g.flag_list[slot] = ((unsigned long long)i << 32) | j;
+                    }
+                    stg[lane * 33 + k] = dist;
+                }
+                __syncwarp();
+                uint64_t tri_row = T2(row0);
+                for (int r = 0; r < 32; ++r) {
+                    const uint32_t ir = row0 + r;
+                    if (ir >= g.n) break;
+                    const uint32_t j = col0 + lane;
+                    if (j <= ir) __stcs(g.out + tri_row + j, stg[r * 33 + lane]);
+                    tri_row += ir + 1;
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
+            if (++acc == 2) {
+                acc = 0;
+                acc_phase ^= 1;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+}
+
+// -------------------------------------------------------------- fixup ----
+// FP64 direct-difference recompute of the flagged pairs.  If the list
+// overflowed, every pair whose stored distance passes a slightly wider
+// version of the flag test is recomputed instead.
+__global__ void fixup_kernel(const float *__restrict__ x, uint32_t n, uint32_t d, float *__restrict__ out,
+                             const float *__restrict__ norms, const unsigned long long *__restrict__ count,
+                             const unsigned long long *__restrict__ list, unsigned long long cap, float tau,
+                             unsigned long long *n_flagged)
+{
+    const unsigned long long cnt = *count;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (uint64_t)gridDim.x * blockDim.x;
+    if (tid == 0 && n_flagged) *n_flagged = cnt;
+    auto recompute = [&](uint32_t i, uint32_t j) {
+        const float *xi = x + (size_t)i * d, *xj = x + (size_t)j * d;
+        double s = 0.0;
+        for (uint32_t k = 0; k < d; ++k) {
+            const double df = (double)xi[k] - (double)xj[k];
+            s = fma(df, df, s);
+        }
+        out[T2(i) + j] = (float)sqrt(s);
+    };
+    if (cnt <= cap) {
+        for (uint64_t e = tid; e < cnt; e += nth) {
+            const unsigned long long v = list[e];
+            recompute((uint32_t)(v >> 32), (uint32_t)(v & 0xFFFFFFFFu));
+        }
+    } else {
+        const uint64_t total = T2(n);
+        const float wide = 1.0625f * tau;
+        for (uint64_t p = tid; p < total; p += nth) {
+            uint32_t i, j;
+            lambda_diag<TRI_SQRT_X>((uint32_t)p, i, j);
+            if (i == j) continue;
+            const float v = out[p];
+            if (v * v < wide * (norms[i] + norms[j])) recompute(i, j);
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+uint32_t num_sms()
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm > 0 ? (uint32_t)nsm : 1;
+}
+
+}  // namespace
+
+size_t trihost::edm_tc_workspace(uint32_t n, uint32_t d, int prec) { return ws_layout(n, d, prec).total; }
+
+namespace {
+
+struct TcPlan {
+    int P;
+    uint32_t dp, nkc, stages;
+    size_t smem;
+};
+
+bool plan(uint32_t d, int prec, TcPlan &p)
+{
+    p.P = prec == TRI_BF16X6 ? 3 : 2;
+    p.dp = (d + KCH - 1) / KCH * KCH;
+    p.nkc = p.dp / KCH;
+    const size_t fixed = 1024 /*align*/ + 4 * EPI_STAGE_FLOATS * 4 + 8 * (7 + 2 * 8);
+    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = (size_t)p.P * CHUNK_BYTES;
+    if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
+    p.stages = (uint32_t)std::min<size_t>(8, (SMEM_LIMIT - fixed - a) / st);
+    p.smem = fixed + a + p.stages * st;
+    return true;
+}
+
+}  // namespace
+
+// Largest n whose packed triangle n(n+1)/2 stays below 2^32 entries (the
+// recompute pass walks it with 32-bit lambda).
+constexpr uint32_t TC_MAX_N = 92681;
+
+extern "C" int tri_edm_prepare(const float *x, uint32_t n, uint32_t d, int prec, void *workspace, size_t ws_bytes,
+                               void *stream)
+{
+    if (!x || n == 0 || d == 0) return TRI_EINVAL;
+    if (n > TC_MAX_N) return TRI_ERANGE;
+    if (prec != TRI_BF16X3 && prec != TRI_BF16X6) return TRI_EINVAL;
+    TcPlan pl;
+    if (!plan(d, prec, pl)) return TRI_ERANGE;
+    const WsLayout L = ws_layout(n, d, prec);
+    if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    if (cudaMemsetAsync(ws, 0, 256, s) != cudaSuccess) return TRI_ECUDA;
+    const unsigned blocks = (unsigned)(((uint64_t)n * 32 + 255) / 256);
+    if (pl.P == 3)
+        prepare_kernel<3><<<blocks, 256, 0, s>>>(x, n, d, pl.dp, (float *)(ws + L.norms),
+                                                 (__nv_bfloat16 *)(ws + L.planes));
+    else
+        prepare_kernel<2><<<blocks, 256, 0, s>>>(x, n, d, pl.dp, (float *)(ws + L.norms),
+                                                 (__nv_bfloat16 *)(ws + L.planes));
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int prec, void *workspace, size_t ws_bytes,
+                            void *stream)
+{
+    if (!out || n == 0 || d == 0) return TRI_EINVAL;
+    if (n > TC_MAX_N) return TRI_ERANGE;
+    if (prec != TRI_BF16X3 && prec != TRI_BF16X6) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    TcPlan pl;
+    if (!plan(d, prec, pl)) return TRI_ERANGE;
+    const WsLayout L = ws_layout(n, d, prec);
+    if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
+    const uint32_t m = (n + TILE - 1) / TILE;
+    const uint64_t ntiles = map == TRI_MAP_LAMBDA ? T2(m) : (uint64_t)m * m;
+    if (ntiles > 0xFFFFFFFFull) return TRI_ERANGE;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return TRI_ECUDA;
+    char *ws = (char *)workspace;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[3] = {pl.dp, n, (cuuint64_t)pl.P};
+    const cuuint64_t gstride[2] = {(cuuint64_t)pl.dp * 2, (cuuint64_t)n * pl.dp * 2};
+    const cuuint32_t box[3] = {KCH, TILE, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws + L.planes, gdim, gstride, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return TRI_ECUDA;
+    GramArgs g{};
+    g.n = n;
+    g.nkc = pl.nkc;
+    g.m = m;
+    g.ntiles = ntiles;
+    g.stages = pl.stages;
+    g.tau = pl.P == 3 ? TAU_X6 : TAU_X3;
+    g.norms = (const float *)(ws + L.norms);
+    g.out = out;
+    g.flag_count = (unsigned long long *)(ws + L.hdr);
+    g.status = (int *)(ws + L.hdr + 8);
+    g.flag_list = (unsigned long long *)(ws + L.flags);
+    g.flag_cap = L.cap;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(num_sms(), ntiles);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+#define TRI_G(MP, PP)                                                                                          \
+    e = cudaFuncSetAttribute(gram_kernel<MP, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);  \
+    if (e == cudaSuccess) gram_kernel<MP, PP><<<grid, NTHREADS, pl.smem, s>>>(tmap, g);
+    if (map == TRI_MAP_LAMBDA) {
+        if (pl.P == 3) {
+            TRI_G(MAP_LAMBDA, 3)
+        } else {
+            TRI_G(MAP_LAMBDA, 2)
+        }
+    } else {
+        if (pl.P == 3) {
+            TRI_G(MAP_BB, 3)
+        } else {
+            TRI_G(MAP_BB, 2)
+        }
+    }
+#undef TRI_G
+    if (e != cudaSuccess) return TRI_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+extern "C" int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out, int prec, void *workspace,
+                             size_t ws_bytes, unsigned long long *n_flagged, void *stream)
+{
+    if (!x || !out || n == 0 || d == 0) return TRI_EINVAL;
+    if (n > TC_MAX_N) return TRI_ERANGE;
+    if (prec != TRI_BF16X3 && prec != TRI_BF16X6) return TRI_EINVAL;
+    const WsLayout L = ws_layout(n, d, prec);
+    if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
+    char *ws = (char *)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    fixup_kernel<<<num_sms() * 4, 256, 0, s>>>(x, n, d, out, (const float *)(ws + L.norms),
+                                               (const unsigned long long *)(ws + L.hdr),
+                                               (const unsigned long long *)(ws + L.flags), L.cap,
+                                               prec == TRI_BF16X6 ? TAU_X6 : TAU_X3, n_flagged);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+int trihost::edm_tc(const float *x, uint32_t n, uint32_t d, float *out, int map, int prec, void *ws,
+                    size_t ws_bytes, unsigned long long *n_flagged, cudaStream_t s)
+{
+    int st = tri_edm_prepare(x, n, d, prec, ws, ws_bytes, s);
+    if (st == TRI_OK) st = tri_edm_gram(n, d, out, map, prec, ws, ws_bytes, s);
+    if (st == TRI_OK) st = tri_edm_fixup(x, n, d, out, prec, ws, ws_bytes, n_flagged, s);
+    return st;
+}

@@ -1,0 +1,202 @@
+"""Python binding of libtri.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (include/tri.h),
+takes torch tensors that already live on the GPU, passes their device pointers
+and the current CUDA stream through the C ABI, and raises TriError on a
+non-zero status.  No step of any computation runs in Python or torch: if the
+shared library is missing this module fails to import.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libtri.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"libtri.so not found at {_LIB_PATH}: build it first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+# ------------------------------------------------------------- constants --
+TRI_OK, TRI_EINVAL, TRI_ERANGE, TRI_ECUDA, TRI_EOVERFLOW, TRI_ETIMEOUT, TRI_ENOSPACE = range(7)
+MAP_LAMBDA, MAP_BB, MAP_RB, MAP_REC, MAP_UTM, MAP_LAMBDA_PDELTA = range(6)
+MAP_NAMES = {MAP_LAMBDA: "lambda", MAP_BB: "bb", MAP_RB: "rb", MAP_REC: "rec", MAP_UTM: "utm",
+             MAP_LAMBDA_PDELTA: "lambda_pdelta"}
+SQRT_X, SQRT_R, SQRT_N = range(3)
+FP32, BF16X3, BF16X6 = range(3)
+BODY_DUMMY, BODY_SENTINEL, BODY_COUNT = range(3)
+LIFE_BIRTH = 1 << 3
+LIFE_SURVIVE = (1 << 2) | (1 << 3)
+
+_u32, _u64, _i32, _sz, _vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
+_f32, _f64 = ctypes.c_float, ctypes.c_double
+_szp = ctypes.POINTER(ctypes.c_size_t)
+
+_SIGS = {
+    "tri_status_string": ([_i32], ctypes.c_char_p),
+    "tri_version": ([], _i32),
+    "tri_map_launch": ([_i32, _i32, _u32, _u32, _i32, _i32, _vp, _vp], _i32),
+    "tri_lambda_verify": ([_i32, _i32, _u64, _u64, _vp, _vp], _i32),
+    "tri_edm": ([_vp, _u32, _u32, _vp, _i32, _u32, _u32, _i32, _vp, _sz, _vp, _vp], _i32),
+    "tri_edm_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
+    "tri_edm_batched": ([_vp, _vp, _vp, _u32, _u32, _vp, _vp, _u32, _u32, _vp, _sz, _vp], _i32),
+    "tri_edm_batched_workspace_size": ([_u32, _szp], _i32),
+    "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
+    "tet_map": ([_u32, _u32, _i32, _vp, _vp], _i32),
+    "tet_at_energy": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp, _sz, _vp], _i32),
+    "tet_at_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
+    "tri_mlp_workspace_size": ([_u32, _u32, _u32, _szp], _i32),
+    "tri_mlp_forward": ([_vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _sz, _vp], _i32),
+    "tri_mlp_grad": ([_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp, _sz, _vp], _i32),
+    "tri_mlp_adam": ([_vp, _vp, _vp, _vp, _u32, _u32, _f32, _f32, _f32, _f32, _vp], _i32),
+    "tri_mlp_argmin": ([_vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _sz, _vp], _i32),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+LIB_PATH = _LIB_PATH
+EXPORTS = tuple(_SIGS)
+
+
+class TriError(RuntimeError):
+    def __init__(self, call: str, status: int):
+        super().__init__(f"{call}: {_lib.tri_status_string(status).decode()} (status {status})")
+        self.status = status
+
+
+def _check(call: str, st: int) -> None:
+    if st != TRI_OK:
+        raise TriError(call, st)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _size(fn, *args) -> int:
+    out = ctypes.c_size_t(0)
+    _check(fn.__name__, fn(*args, ctypes.byref(out)))
+    return int(out.value)
+
+
+def tri_version() -> int:
+    return int(_lib.tri_version())
+
+
+# ------------------------------------------------------------------ maps --
+def tri_map_launch(map: int, sqrt_kind: int, n: int, rho: int, with_diag: bool, body: int, out,
+                   stream=None) -> None:
+    _check("tri_map_launch", _lib.tri_map_launch(map, sqrt_kind, n, rho, 1 if with_diag else 0, body,
+                                                 _ptr(out), _stream(stream)))
+
+
+def tri_lambda_verify(sqrt_kind: int, with_diag: bool, w_begin: int, w_end: int, result, stream=None) -> None:
+    _check("tri_lambda_verify", _lib.tri_lambda_verify(sqrt_kind, 1 if with_diag else 0, w_begin, w_end,
+                                                       _ptr(result), _stream(stream)))
+
+
+def tet_map(n: int, rho: int, body: int, out, stream=None) -> None:
+    _check("tet_map", _lib.tet_map(n, rho, body, _ptr(out), _stream(stream)))
+
+
+# ------------------------------------------------------------------- EDM --
+def tri_edm_workspace_size(n: int, d: int, prec: int) -> int:
+    return _size(_lib.tri_edm_workspace_size, n, d, prec)
+
+
+def tri_edm(x, out, map: int = MAP_LAMBDA, rho: int = 16, reg: int = 0, prec: int = FP32, workspace=None,
+            n_flagged=None, stream=None) -> None:
+    n, d = x.shape
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("tri_edm", _lib.tri_edm(_ptr(x), n, d, _ptr(out), map, rho, reg, prec, _ptr(workspace), ws_bytes,
+                                   _ptr(n_flagged), _stream(stream)))
+
+
+def tri_edm_batched_workspace_size(count: int) -> int:
+    return _size(_lib.tri_edm_batched_workspace_size, count)
+
+
+def tri_edm_batched(x_cat, pt_off, n_k, out_cat, out_off, rho: int = 16, reg: int = 0, workspace=None,
+                    stream=None) -> None:
+    count = n_k.numel()
+    d = x_cat.shape[1]
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("tri_edm_batched", _lib.tri_edm_batched(_ptr(x_cat), _ptr(pt_off), _ptr(n_k), count, d,
+                                                   _ptr(out_cat), _ptr(out_off), rho, reg, _ptr(workspace),
+                                                   ws_bytes, _stream(stream)))
+
+
+# -------------------------------------------------------------------- CA --
+def tri_ca_step(inp, out, n: int, birth_mask: int = LIFE_BIRTH, survive_mask: int = LIFE_SURVIVE,
+                map: int = MAP_LAMBDA, rho: int = 16, stream=None) -> None:
+    ld = inp.stride(0)
+    if out.stride(0) != ld:
+        raise ValueError("in and out must share the leading dimension")
+    _check("tri_ca_step", _lib.tri_ca_step(_ptr(inp), _ptr(out), n, ld, birth_mask, survive_mask, map, rho,
+                                           _stream(stream)))
+
+
+# -------------------------------------------------------------------- AT --
+def tet_at_workspace_size(n: int, rho: int, map: int = MAP_LAMBDA) -> int:
+    return _size(_lib.tet_at_workspace_size, n, rho, map)
+
+
+def tet_at_energy(xyz, energy, nu: float = 1.0, map: int = MAP_LAMBDA, rho: int = 16, workspace=None,
+                  stream=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("tet_at_energy", _lib.tet_at_energy(_ptr(xyz), xyz.shape[0], float(nu), _ptr(energy), map, rho,
+                                               _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+# ------------------------------------------------------------------- MLP --
+def tri_mlp_workspace_size(B: int, H1: int, H2: int) -> int:
+    return _size(_lib.tri_mlp_workspace_size, B, H1, H2)
+
+
+def _ws(workspace):
+    return _ptr(workspace), workspace.numel() * workspace.element_size()
+
+
+def tri_mlp_forward(theta, X, pred, H1: int, H2: int, workspace, stream=None) -> None:
+    B, F = X.shape
+    p, nb = _ws(workspace)
+    _check("tri_mlp_forward", _lib.tri_mlp_forward(_ptr(theta), _ptr(X), B, F, H1, H2, _ptr(pred), p, nb,
+                                                   _stream(stream)))
+
+
+def tri_mlp_grad(theta, X, y, loss, grad, H1: int, H2: int, workspace, stream=None) -> None:
+    B, F = X.shape
+    p, nb = _ws(workspace)
+    _check("tri_mlp_grad", _lib.tri_mlp_grad(_ptr(theta), _ptr(X), _ptr(y), B, F, H1, H2, _ptr(loss),
+                                             _ptr(grad), p, nb, _stream(stream)))
+
+
+def tri_mlp_adam(theta, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8, stream=None) -> None:
+    _check("tri_mlp_adam", _lib.tri_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), theta.numel(), t, lr,
+                                             beta1, beta2, eps, _stream(stream)))
+
+
+def tri_mlp_argmin(theta, X, best, H1: int, H2: int, workspace, stream=None) -> None:
+    B, F = X.shape
+    p, nb = _ws(workspace)
+    _check("tri_mlp_argmin", _lib.tri_mlp_argmin(_ptr(theta), _ptr(X), B, F, H1, H2, _ptr(best), p, nb,
+                                                 _stream(stream)))

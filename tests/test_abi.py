@@ -1,0 +1,68 @@
+"""The C ABI library builds, loads and exports every entry point of include/tri.h (no GPU calls)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tri.h")).read()
+    return sorted(set(re.findall(r"^TRI_API\s+[\w\s\*]*?\b((?:tri|tet)_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1609_01490_gb300 import build
+    build.build()
+    return build.LIB
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("tri_map_launch", "tri_edm", "tri_ca_step", "tet_map", "tet_at_energy", "tri_edm_batched",
+                 "tri_mlp_grad", "tri_lambda_verify"):
+        assert must in names
+
+
+def test_exports_match_header(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert set(_declared()) <= exported
+    # nothing but the declared entry points leaks out of the library
+    assert {e for e in exported if e.startswith(("tri_", "tet_"))} == set(_declared())
+
+
+def test_binding_loads_without_gpu(lib):
+    pytest.importorskip("torch")
+    from paper_1609_01490_gb300 import tri
+    assert tri.tri_version() == 10000
+    assert set(tri.EXPORTS) >= set(_declared())
+    assert tri.tri_edm_workspace_size(100, 3, tri.FP32) == 0
+    assert tri.tet_at_workspace_size(96, 8) == 8 * (12 * 13 * 14 // 6)
+    assert tri.tri_edm_batched_workspace_size(10) >= 8 * 11
+    with pytest.raises(tri.TriError):
+        tri.tet_at_workspace_size(96, 7)
+
+
+def test_host_side_argument_errors(lib):
+    # argument checks run on the host before any launch, so they need no GPU
+    import ctypes
+    L = ctypes.CDLL(lib)
+    L.tri_map_launch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    dummy = ctypes.c_void_p(16)
+    assert L.tri_map_launch(0, 1, 100, 7, 1, 0, dummy, None) == 1          # rho 7
+    assert L.tri_map_launch(0, 1, 0, 16, 1, 0, dummy, None) == 1           # n = 0
+    assert L.tri_map_launch(0, 1, 100, 16, 1, 0, None, None) == 1          # null out
+    assert L.tri_map_launch(9, 1, 100, 16, 1, 0, dummy, None) == 1         # unknown map
+    assert L.tri_map_launch(3, 1, 100, 16, 1, 0, dummy, None) == 2         # REC needs 2^k blocks
+    assert L.tri_map_launch(0, 1, 4000000, 8, 1, 0, dummy, None) == 2      # > 2^32 blocks
+    L.tri_ca_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t,
+                              ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p]
+    assert L.tri_ca_step(dummy, dummy, 64, 64, 8, 12, 0, 16, None) == 1   # aliasing
+    assert L.tri_ca_step(ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), 64, 60, 8, 12, 0, 16, None) == 1  # ld
+    L.tri_status_string.restype = ctypes.c_char_p
+    assert b"TRI_ERANGE" in L.tri_status_string(2)
