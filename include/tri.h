@@ -225,6 +225,31 @@ TRI_API int tet_at_energy(const float *xyz, uint32_t n, double nu, double *energ
 TRI_API int tet_at_workspace_size(uint32_t n, uint32_t rho, int map, size_t *bytes);
 
 /*
+ * tet_at_energy_noalloc -- tet_at_energy without a workspace, for callers
+ * that cannot call cudaMalloc: code whose device memory is all handed out by
+ * another allocator (a framework's caching pool, an arena fixed at start-up)
+ * and code that must not trigger the device-wide synchronisation cudaMalloc
+ * and cudaFree can imply.  The paper has no counterpart; this is a property
+ * of the library, not of the method.
+ *   The block partials live in a 2 MiB array (262,144 doubles) compiled into
+ *   libtri.so, which every GPU that loads the library holds until the process
+ *   exits.  Sizes whose partial count T_m, m = ceil(n/rho), exceeds it are
+ *   rejected with TRI_ENOSPACE (n <= 920 at rho = 8, 1840 at rho = 16, 3680
+ *   at rho = 32).  Allocates nothing: no cudaMalloc, cudaFree or allocating
+ *   library call.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls share the one array: calls whose kernels may overlap on the GPU
+ *   (different streams, or host threads without ordering between them) race
+ *   on it and must be serialised by the caller.  Nothing in it has to start
+ *   at zero: each call writes every partial it reads.
+ *   Arguments, result and other errors as in tet_at_energy.
+ */
+TRI_API int tet_at_energy_noalloc(const float *xyz, uint32_t n, double nu, double *energy, int map,
+                                  uint32_t rho, void *stream);
+
+/*
  * MLP cost model y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 (one output), used
  * to predict the log run time of a (kernel, n, d, map, rho) configuration.
  * Not in the paper.  theta (device FP32) holds W1 [H1][F], b1 [H1],

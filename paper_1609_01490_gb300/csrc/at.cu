@@ -134,3 +134,59 @@ extern "C" int tet_at_energy(const float *xyz, uint32_t n, double nu, double *en
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 7)) return TRI_ENOSPACE;
     return at_energy_launch(xyz, n, nu, energy, map, rho, (double *)workspace, (cudaStream_t)stream);
 }
+
+// ---------------------------------------------------------------------------
+// tet_at_energy_noalloc: the same energy with no workspace argument.
+//
+// Some callers cannot call cudaMalloc when they need this energy: code whose
+// device memory is all handed out by another allocator (a framework's caching
+// pool or a fixed arena sized at start-up), and code that must not trigger the
+// device-wide synchronisation that cudaMalloc and cudaFree can imply.  For
+// them the block partials live in an array compiled into the library
+// (AT_STATIC_PARTIALS doubles, 2 MiB), which every GPU that loads the library
+// holds until the process exits.  The caller still owns the points and the
+// result.
+#include <mutex>
+
+namespace {
+
+constexpr size_t AT_STATIC_PARTIALS = size_t(1) << 18;  // 262,144 doubles = 2 MiB
+static __device__ __align__(256) double g_at_partials[AT_STATIC_PARTIALS];
+
+constexpr int AT_MAX_DEVICES = 64;
+std::mutex g_at_mu;
+double *g_at_ptr[AT_MAX_DEVICES] = {};
+
+// Device address of g_at_partials on the current device, looked up once per
+// device with that device current (host code cannot use the symbol itself).
+int at_static_partials(double **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= AT_MAX_DEVICES) return TRI_ECUDA;
+    std::lock_guard<std::mutex> lock(g_at_mu);
+    if (!g_at_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_at_partials) != cudaSuccess || !p) return TRI_ECUDA;
+        g_at_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_at_ptr[dev];
+    return TRI_OK;
+}
+
+}  // namespace
+
+extern "C" int tet_at_energy_noalloc(const float *xyz, uint32_t n, double nu, double *energy, int map, uint32_t rho,
+                                     void *stream)
+{
+    if (!xyz || !energy || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    size_t need = 0;
+    tet_at_workspace_size(n, rho, map, &need);
+    if (need > sizeof(double) * AT_STATIC_PARTIALS) return TRI_ENOSPACE;  // more blocks than the array holds
+    double *partial = nullptr;
+    const int st = at_static_partials(&partial);
+    if (st != TRI_OK) return st;
+    // Every partial the reduction reads is written by this call's first
+    // kernel, so nothing in the array needs clearing between calls.
+    return at_energy_launch(xyz, n, nu, energy, map, rho, partial, (cudaStream_t)stream);
+}

@@ -51,6 +51,7 @@ _SIGS = {
     "tet_map": ([_u32, _u32, _i32, _vp, _vp], _i32),
     "tet_at_energy": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp, _sz, _vp], _i32),
     "tet_at_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
+    "tet_at_energy_noalloc": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp], _i32),
     "tri_mlp_workspace_size": ([_u32, _u32, _u32, _szp], _i32),
     "tri_mlp_forward": ([_vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _sz, _vp], _i32),
     "tri_mlp_grad": ([_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp, _sz, _vp], _i32),
@@ -164,6 +165,14 @@ def tet_at_energy(xyz, energy, nu: float = 1.0, map: int = MAP_LAMBDA, rho: int 
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("tet_at_energy", _lib.tet_at_energy(_ptr(xyz), xyz.shape[0], float(nu), _ptr(energy), map, rho,
                                                _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def tet_at_energy_noalloc(xyz, energy, nu: float = 1.0, map: int = MAP_LAMBDA, rho: int = 16,
+                          stream=None) -> None:
+    """tet_at_energy with its scratch in an array inside the library, for
+    callers that cannot allocate device memory (see include/tri.h)."""
+    _check("tet_at_energy_noalloc", _lib.tet_at_energy_noalloc(_ptr(xyz), xyz.shape[0], float(nu), _ptr(energy),
+                                                               map, rho, _stream(stream)))
 
 
 # ------------------------------------------------------------------- MLP --
