@@ -158,14 +158,18 @@ def run_reference(args, rank: int, world: int):
 
 # -------------------------------------------------------------- our arm -----
 def main():
+    global N_PTS, D_FEAT, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3", "bf16x6"])
+    ap.add_argument("--prec", default="bf16x6", choices=["fp32", "bf16x3", "bf16x6"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--no-arms", action="store_true", help="skip the BB and FP32 comparison arms")
+    ap.add_argument("--n", type=int, default=N_PTS, help="points (smaller cases are for profiling only)")
+    ap.add_argument("--d", type=int, default=D_FEAT, help="features (smaller cases are for profiling only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -176,6 +180,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if (args.n, args.d) != (N_PTS, D_FEAT):
+        N_PTS, D_FEAT = args.n, args.d
+        WORKLOAD = f"edm_n{N_PTS}_d{D_FEAT}_normal_dup1pct"
 
     import torch
     import torch.distributed as dist
@@ -191,19 +198,34 @@ def main():
         if world > 1:
             dist.barrier()
 
-    prec = {"fp32": tri.FP32, "bf16x3": tri.BF16X3, "bf16x6": tri.BF16X6}[args.prec]
+    PRECS = {"fp32": tri.FP32, "bf16x3": tri.BF16X3, "bf16x6": tri.BF16X6}
+    prec = PRECS[args.prec]
     x_host = inputs.edm_normal_points(N_PTS, D_FEAT, seed=1609 + rank, dup_frac=DUP)
     P = N_PTS * (N_PTS + 1) // 2
     x = torch.from_numpy(x_host).to(dev)
     out = torch.empty(P, dtype=torch.float32, device=dev)
-    ws_bytes = tri.tri_edm_workspace_size(N_PTS, D_FEAT, prec)
-    ws = torch.empty(max(ws_bytes, 16), dtype=torch.uint8, device=dev)
+    ws_bytes = max(tri.tri_edm_workspace_size(N_PTS, D_FEAT, p) for p in PRECS.values())
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
     flagged = torch.zeros(1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
+    phase_events = []  # (prepare, gram, fixup) event pairs recorded inside the timed region
 
-    def step(map_id, out_t=out, x_t=x):
-        tri.tri_edm(x_t, out_t, map=map_id, rho=16, reg=4, prec=prec,
-                    workspace=ws if ws_bytes else None, n_flagged=flagged if prec != tri.FP32 else None)
+    def step(map_id, pr=prec, record=False):
+        if pr == tri.FP32:
+            tri.tri_edm(x, out, map=map_id, rho=16, reg=4, prec=pr)
+            return
+        if not record:
+            tri.tri_edm(x, out, map=map_id, prec=pr, workspace=ws, n_flagged=flagged)
+            return
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        tri.tri_edm_prepare(x, pr, ws)
+        ev[1].record(stream)
+        tri.tri_edm_gram(N_PTS, D_FEAT, out, map_id, pr, ws)
+        ev[2].record(stream)
+        tri.tri_edm_fixup(x, out, pr, ws, flagged)
+        ev[3].record(stream)
+        phase_events.append(ev)
 
     def timed(fn, k, w):
         for _ in range(w):
@@ -220,24 +242,38 @@ def main():
         return ev0.elapsed_time(ev1) / k  # ms per step
 
     # ---- headline: lambda map, timed region with clock sampling
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler = ClockSampler(local)
     for _ in range(args.warmup):
         step(tri.MAP_LAMBDA)
     barrier()
     torch.cuda.synchronize()
     sampler.start()
-    ms_lambda = timed(lambda: step(tri.MAP_LAMBDA), args.steps, 0)
+    ms_lambda = timed(lambda: step(tri.MAP_LAMBDA, record=True), args.steps, 0)
     clocks = sampler.stop()
     ms_t = torch.tensor([ms_lambda], device=dev)
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms_step = float(ms_t.item())
     value = world * P / (ms_step * 1e-3)
+    n_flagged = int(flagged.item())
+    phases = None
+    if phase_events:
+        tot = [0.0, 0.0, 0.0]
+        for ev in phase_events:
+            for q in range(3):
+                tot[q] += ev[q].elapsed_time(ev[q + 1])
+        phases = {"prepare_ms": tot[0] / len(phase_events), "gram_ms": tot[1] / len(phase_events),
+                  "fixup_ms": tot[2] / len(phase_events)}
 
     # ---- bounding box on the same input (the paper's I = t_BB / t_lambda)
-    ms_bb = timed(lambda: step(tri.MAP_BB), max(3, args.steps // 2), 2)
+    ms_bb = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_BB), max(3, args.steps // 2), 2)
+    # ---- the FP32 direct-difference path on the same input, for comparison
+    if prec == tri.FP32:
+        ms_fp32 = ms_step
+    else:
+        ms_fp32 = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_LAMBDA, tri.FP32), 3, 1)
 
-    # ---- roofline of the dominant kernel (one kernel per FP32 step)
+    # ---- roofline of the dominant kernel
     peaks, peak_src = load_peaks()
     clk = float(peaks.get("sm_max_mhz", 2070.0))
     if prec == tri.FP32:
@@ -247,8 +283,27 @@ def main():
         roof = {"bound": "alu", "kernel": "edm_kernel<lambda,16,4>", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz (derived)"}
+        roof_alt = None
     else:
-        roof = None
+        nprod = 6 if prec == tri.BF16X6 else 3
+        planes = 3 if prec == tri.BF16X6 else 2
+        dp = -(-D_FEAT // 64) * 64
+        t_gram = phases["gram_ms"] * 1e-3
+        # algorithmic bytes: the packed FP32 triangle written once, the planes and norms read once
+        nbytes = 4.0 * P + planes * N_PTS * dp * 2 + 4 * N_PTS
+        hbm = nbytes / t_gram / 1e9
+        tiles = (-(-N_PTS // 128)) * (-(-N_PTS // 128) + 1) // 2
+        tflop = 2.0 * dp * nprod * tiles * 128 * 128 / t_gram / 1e12
+        roof_hbm = {"bound": "hbm", "kernel": f"gram_kernel<lambda,{planes}>", "achieved": hbm,
+                    "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": hbm / float(peaks["hbm_gbs"]),
+                    "traffic": None, "algorithmic_bytes": nbytes,
+                    "peak_source": f"hbm_gbs of {peak_src}"}
+        roof_tc = {"bound": "tensor", "kernel": f"gram_kernel<lambda,{planes}>", "achieved": tflop,
+                   "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
+                   "frac": tflop / float(peaks["bf16_tflops"]), "traffic": None,
+                   "flops": 2.0 * dp * nprod * tiles * 128 * 128,
+                   "peak_source": f"bf16_tflops (burst) of {peak_src}"}
+        roof, roof_alt = (roof_hbm, roof_tc) if roof_hbm["frac"] >= roof_tc["frac"] else (roof_tc, roof_hbm)
 
     # ---- end to end through host buffers: pinned H2D of x, tri_edm, D2H of the triangle
     e2e = None
@@ -271,13 +326,19 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "bf16x6": "bf16"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP, "map": "lambda", "rho": 16,
-                   "reg": 4, "prec": args.prec, "pairs_per_step": P,
+        "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP, "map": "lambda",
+                   "tile": "16x16 threads x 4x4 pairs" if prec == tri.FP32 else "128x128 tcgen05 tiles",
+                   "prec": args.prec, "pairs_per_step": P,
                    "l2": "each step writes the 8.59 GB triangle (> 129 MB L2), which flushes L2 between steps"},
         "bb": {"ms_per_step": ms_bb, "value": world * P / (ms_bb * 1e-3), "I_bb_over_lambda": ms_bb / ms_step},
+        "fp32_lambda": {"ms_per_step": ms_fp32, "value": world * P / (ms_fp32 * 1e-3),
+                        "speedup_of_headline": ms_fp32 / ms_step},
         "clocks": clocks,
-        "gpu_launches": args.steps * 1,
+        "gpu_launches": args.steps * (1 if prec == tri.FP32 else 3),
         "roofline": roof,
+        "roofline_other": roof_alt,
+        "phases": phases,
+        "n_flagged": n_flagged if prec != tri.FP32 else None,
         "peaks": {"source": peak_src},
     }
     if e2e:

@@ -140,7 +140,7 @@ TRI_API int tri_lambda_verify(int sqrt_kind, int with_diag, uint64_t w_begin, ui
  *   S x S pair tile, S = rho*reg, placed by `map` (any tri_map).  No workspace.
  *   prec = TRI_BF16X3 / TRI_BF16X6: 128 x 128 pair tiles on tcgen05 tensor
  *   cores, placed by TRI_MAP_LAMBDA or TRI_MAP_BB; rho and reg are ignored;
- *   needs `workspace` of tri_edm_workspace_size bytes (16-byte aligned).
+ *   needs `workspace` of tri_edm_workspace_size bytes (256-byte aligned).
  *   Pairs whose Gram estimate of d^2 falls below tau*(|x_i|^2 + |x_j|^2) are
  *   recomputed in FP64 by direct differences; n_flagged (device uint64,
  *   may be NULL) receives how many were flagged.  If more were flagged than
@@ -155,6 +155,35 @@ TRI_API int tri_edm(const float *x, uint32_t n, uint32_t d, float *out, int map,
 
 /* Workspace bytes tri_edm needs for (n, d, prec); 0 for TRI_FP32. */
 TRI_API int tri_edm_workspace_size(uint32_t n, uint32_t d, int prec, size_t *bytes);
+
+/*
+ * The three phases of tri_edm for prec = TRI_BF16X3 / TRI_BF16X6, callable on
+ * their own (same stream, in this order) to time them or to reuse prepared
+ * operands.  workspace: tri_edm_workspace_size bytes, 256-byte aligned.
+ * Tensor-core limits: n <= 92681 (packed triangle below 2^32 entries),
+ * d <= 192 for BF16X6 and d <= 320 for BF16X3 (the split planes of one row
+ * block stay resident in shared memory); larger sizes give TRI_ERANGE.
+ *
+ *   tri_edm_prepare: clears the workspace header, then writes the FP32 row
+ *     norms |x_i|^2 (summed in FP64) and the BF16 split planes (hi, lo or hi,
+ *     mid, lo; K zero-padded to a multiple of 64).
+ *   tri_edm_gram: tensor-core Gram term, d^2 = |x_i|^2 + |x_j|^2 - 2 x_i.x_j,
+ *     clamped at 0, square root stored to out (packed, FP32); pairs with
+ *     d^2 < tau (|x_i|^2 + |x_j|^2) appended to the workspace's flag list.
+ *     map: TRI_MAP_LAMBDA (tiles in lambda order) or TRI_MAP_BB.  A device
+ *     wait that exceeds 2 s sets the workspace status word to TRI_ETIMEOUT
+ *     and the kernel returns.
+ *   tri_edm_fixup: recomputes the flagged pairs in FP64 by direct differences
+ *     (or, when the list overflowed, every pair whose stored distance passes a
+ *     slightly wider flag test) and writes the flag count to *n_flagged
+ *     (device uint64, may be NULL).
+ */
+TRI_API int tri_edm_prepare(const float *x, uint32_t n, uint32_t d, int prec, void *workspace,
+                            size_t ws_bytes, void *stream);
+TRI_API int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int prec, void *workspace,
+                         size_t ws_bytes, void *stream);
+TRI_API int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out, int prec, void *workspace,
+                          size_t ws_bytes, unsigned long long *n_flagged, void *stream);
 
 /*
  * tri_edm_batched -- many EDM triangles of uneven size in one persistent

@@ -17,10 +17,13 @@
 // pair tiles taken in lambda order (Eq. eq_gmap) as one contiguous run of
 // tile numbers per CTA, so consecutive tiles share their row block and the
 // CTA keeps that row block's planes (A) resident in shared memory while TMA
-// streams the column blocks (B) through a ring of stages.  Warp 0 issues TMA,
-// warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator, warps
-// 2-5 read TMEM back, form the distances, flag cancellations and store the
-// packed rows.  fixup: FP64 recompute of the flagged pairs.
+// streams the column blocks (B) through a ring of 16 KB stages, one per
+// (64-wide K chunk, plane).  Warp 0 issues TMA,
+// warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator (with the
+// column block as the M operand, so TMEM lanes are output columns), warps
+// 2-17 read TMEM back, form the distances, flag cancellations and store each
+// packed row segment with one coalesced store per warp.  fixup: FP64
+// recompute of the flagged pairs.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,9 +41,11 @@ namespace {
 constexpr int TILE = 128;                  // pair tile side (UMMA M = N = 128)
 constexpr int KCH = 64;                    // K per chunk: one 128-byte swizzle row of BF16
 constexpr int CHUNK_BYTES = TILE * KCH * 2;  // 16 KB: 128 rows x 64 BF16
-constexpr int NTHREADS = 192;              // 6 warps
-constexpr int EPI_STAGE_FLOATS = 32 * 33;  // per epilogue warp transposition buffer
-constexpr uint32_t SPIN_LIMIT = 1u << 24;  // bounded waits (with nanosleep: well over a second)
+constexpr int NEPI = 16;                   // epilogue warps: 4 TMEM lane quarters x 4 row groups
+constexpr int NTHREADS = 64 + 32 * NEPI;   // TMA warp, MMA warp, epilogue warps
+constexpr int EPI_ROWS = 16;               // output rows per TMEM load in the epilogue
+constexpr int NORM_FLOATS = 2 * TILE;      // per epilogue warp: row norms of the tile (double buffered)
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 constexpr int SMEM_LIMIT = 227 * 1024;
 
 constexpr float TAU_X6 = 0.3125f;  // flag threshold for hi/mid/lo (derived bound)
@@ -102,20 +107,38 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Wait for the phase of the given parity to complete.  Gives up after
-// SPIN_LIMIT polls, or early when another role has already given up (unless
+// WAIT_LIMIT_NS, or early when another role has already given up (unless
 // abort_flag is null: the drain waits at exit must not cut short a copy or
 // MMA that is still writing).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
 {
-    for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t start = global_ns();
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
-        if ((it & 63) == 63) {
+        if ((it & 15) == 0) {
             if (abort_flag && *abort_flag) return false;
-            __nanosleep(128);
+            if (global_ns() - start > WAIT_LIMIT_NS) return false;
+            __nanosleep(64);
         }
     }
-    return false;
+}
+
+// mbar_wait by lane 0 with the result broadcast, so the whole warp leaves
+// together and agrees on it.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    int r = 0;
+    if ((threadIdx.x & 31) == 0) r = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, r, 0) != 0;
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
@@ -126,19 +149,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "[%5];" ::"r"(dst),
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (start, leading and stride offsets in 16-byte units).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
-    return d;
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
@@ -165,21 +175,26 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// 32 TMEM lanes x 16 columns: thread t receives lane (base + t), 16 columns.
+// The load is asynchronous: tmem_wait16 must run before the registers are read.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 {
-    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Completes the outstanding TMEM loads.  The registers pass through the asm
+// as read-write operands, so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])::"memory");
 }
 
 // ------------------------------------------------------------ prepare ----
@@ -238,26 +253,48 @@ __device__ __forceinline__ bool tile_of(uint64_t t, uint32_t m, uint32_t &bi, ui
     }
 }
 
-// Products (A plane, B plane) kept by the split: P = 3 -> 6 products, P = 2 -> 3.
-__device__ __constant__ uint8_t kProdA[6] = {0, 0, 1, 0, 2, 1};
-__device__ __constant__ uint8_t kProdB[6] = {0, 1, 0, 2, 0, 1};
+// The split keeps the products of row plane pa and column plane pb with
+// pa + pb <= P - 1: hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid for P = 3
+// and hi.hi, hi.lo, lo.hi for P = 2.
+
+// 1/sqrt by the MUFU unit (flush-to-zero approximation; relative error a few
+// 2^-23, far inside the 1e-5 the distances are held to).
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Shared-memory matrix descriptor of a K-major operand with 128-byte swizzle:
+// start address (bits 0-13) and leading byte offset (bits 16-29, unused for
+// swizzled K-major) in 16-byte units form the low word; the high word holds
+// the stride byte offset (8 rows x 128 B = 1024 B between 8-row groups), the
+// descriptor version for tcgen05 and the swizzle mode, all constant here.
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr) { return (addr >> 4) | (1u << 16); }
+constexpr uint32_t kDescHi = (1024u >> 4) | (1u << 14) | (2u << 29);  // SBO, version, 128-byte swizzle
+
+__device__ __forceinline__ void umma_bf16_lo(uint32_t tmem_d, uint32_t a_lo, uint32_t b_lo, uint32_t accumulate)
+{
+    const uint64_t a = ((uint64_t)kDescHi << 32) | a_lo, b = ((uint64_t)kDescHi << 32) | b_lo;
+    umma_bf16(tmem_d, a, b, accumulate);
+}
 
 template <int MAP, int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_kernel(const __grid_constant__ CUtensorMap tmap, const GramArgs g)
 {
-    constexpr int NPROD = P == 3 ? 6 : 3;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned operand area
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;
-    const uint32_t stage_bytes = (uint32_t)P * CHUNK_BYTES;
+    const uint32_t stage_bytes = CHUNK_BYTES;
     const uint32_t sA = base;                                  // [kc][p] chunks
-    const uint32_t sB = base + a_bytes;                        // [stage][p] chunks
+    const uint32_t sB = base + a_bytes;                        // [stage] chunks, one (K chunk, plane) each
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(epi + 4 * EPI_STAGE_FLOATS);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(epi + NEPI * NORM_FLOATS);
     // barriers: fullA, freeA, done, tmem_full[2], tmem_empty[2], fullB[stages], emptyB[stages]
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t b_fullA = bar0, b_freeA = bar0 + 8, b_done = bar0 + 16;
@@ -274,7 +311,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(b_done, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
-            mbar_init(b_tempty + 8 * i, 4);  // one arrival per epilogue warp
+            mbar_init(b_tempty + 8 * i, NEPI);  // one arrival per epilogue warp
         }
         for (uint32_t s = 0; s < g.stages; ++s) {
             mbar_init(b_fullB + 8 * s, 1);
@@ -297,128 +334,173 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint64_t t0 = (uint64_t)blockIdx.x * per;
     const uint64_t t1 = t0 + per < g.ntiles ? t0 + per : g.ntiles;
 
+    // The TMA and MMA roles run as whole warps: every lane walks the same
+    // loop (so tile, stage and descriptor values stay warp-uniform) and one
+    // lane issues the copies, MMAs and commits.
+    const bool leader = lane == 0;
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
-            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0;
-            uint32_t issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            bool ok = true;
-            for (uint64_t t = t0; t < t1 && ok; ++t) {
-                uint32_t bi, bj;
-                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
-                if (bi != a_row) {
-                    if (a_loads > 0 && !mbar_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
+        if (leader) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+        uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, loads = 0;
+        bool ok = true;
+        for (uint64_t t = t0; t < t1 && ok; ++t) {
+            uint32_t bi, bj;
+            if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+            if (bi != a_row) {
+                if (a_loads > 0 && !warp_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                if (leader) {
                     mbar_expect_tx(b_fullA, a_bytes);
                     for (uint32_t kc = 0; kc < g.nkc; ++kc)
                         for (int p = 0; p < P; ++p)
                             tma_load_3d(sA + (kc * P + p) * CHUNK_BYTES, &tmap, b_fullA, kc * KCH, bi * TILE, p);
-                    ++a_loads;
-                    a_row = bi;
                 }
-                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
-                    if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
+                ++a_loads;
+                a_row = bi;
+            }
+            for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
+                for (int p = 0; p < P; ++p) {  // one stage per (K chunk, plane) of the column block
+                    if (!warp_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(b_fullB + 8 * stage, stage_bytes);
-                    for (int p = 0; p < P; ++p)
-                        tma_load_3d(sB + (stage * P + p) * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH,
-                                    bj * TILE, p);
-                    ++issued[stage];
+                    if (leader) {
+                        mbar_expect_tx(b_fullB + 8 * stage, CHUNK_BYTES);
+                        tma_load_3d(sB + stage * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH, bj * TILE, p);
+                    }
+                    ++loads;
                     if (++stage == g.stages) {
                         stage = 0;
                         b_phase ^= 1;
                     }
                 }
             }
-            if (!ok) {
-                s_abort = 1;
-                atomicExch(g.status, (int)TRI_ETIMEOUT);
-            }
-            // never leave a copy in flight: wait for the last load of every stage
-            for (uint32_t s = 0; s < g.stages; ++s)
-                if (issued[s]) mbar_wait(b_fullB + 8 * s, (issued[s] - 1) & 1, nullptr);
-            if (a_loads) mbar_wait(b_fullA, (a_loads - 1) & 1, nullptr);
         }
+        if (!ok && leader) {
+            s_abort = 1;
+            atomicExch(g.status, (int)TRI_ETIMEOUT);
+        }
+        // never leave a copy in flight: wait for the last load into every
+        // stage (load k went to stage k % stages, in phase k / stages)
+        for (uint32_t st = 0; st < g.stages && st < loads; ++st) {
+            const uint32_t last = loads - 1 - ((loads - 1 - st) % g.stages);
+            warp_wait(b_fullB + 8 * st, (last / g.stages) & 1, nullptr);
+        }
+        if (a_loads) warp_wait(b_fullA, (a_loads - 1) & 1, nullptr);
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, acc = 0, acc_phase = 0;
-            bool ok = true, any = false;
-            for (uint64_t t = t0; t < t1 && ok; ++t) {
-                uint32_t bi, bj;
-                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
-                if (bi != a_row) {
-                    if (a_loads > 0) umma_commit(b_freeA);  // old A is free once issued MMAs finish
-                    if (!mbar_wait(b_fullA, a_loads & 1, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    ++a_loads;
-                    a_row = bi;
-                }
-                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort)) {
+        uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, acc = 0, acc_phase = 0;
+        bool ok = true;
+        for (uint64_t t = t0; t < t1 && ok; ++t) {
+            uint32_t bi, bj;
+            if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+            if (bi != a_row) {
+                if (a_loads > 0 && leader) umma_commit(b_freeA);  // old A is free once issued MMAs finish
+                if (!warp_wait(b_fullA, a_loads & 1, &s_abort)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem + acc * TILE;
-                uint32_t accumulate = 0;
-                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
-                    if (!mbar_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
+                ++a_loads;
+                a_row = bi;
+            }
+            if (!warp_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem + acc * TILE;
+            uint32_t accumulate = 0;
+            for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
+                const uint32_t a_lo = sdesc_lo(sA + kc * P * CHUNK_BYTES);
+#pragma unroll
+                for (int pb = 0; pb < P; ++pb) {
+                    if (!warp_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    const uint32_t b_lo = sdesc_lo(sB + stage * CHUNK_BYTES);
+                    if (leader) {
 #pragma unroll
-                    for (int q = 0; q < NPROD; ++q) {
-                        const uint32_t a_chunk = sA + (kc * P + kProdA[q]) * CHUNK_BYTES;
-                        const uint32_t b_chunk = sB + (stage * P + kProdB[q]) * CHUNK_BYTES;
+                        for (int pa = 0; pa + pb < P; ++pa) {
 #pragma unroll
-                        for (int kk = 0; kk < KCH / 16; ++kk) {
-                            umma_bf16(d_tmem, sdesc(a_chunk + kk * 32), sdesc(b_chunk + kk * 32), accumulate);
-                            accumulate = 1;
+                            for (int kk = 0; kk < KCH / 16; ++kk) {
+                                // the column tile is the M operand: TMEM lane = output column;
+                                // +2 per 16-element K step (32 bytes in 16-byte units)
+                                umma_bf16_lo(d_tmem, b_lo + 2 * kk, a_lo + pa * (CHUNK_BYTES >> 4) + 2 * kk,
+                                             accumulate);
+                                accumulate = 1;
+                            }
                         }
+                        umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
                     }
-                    umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
+                    accumulate = 1;
                     if (++stage == g.stages) {
                         stage = 0;
                         b_phase ^= 1;
                     }
                 }
-                if (!ok) break;
-                umma_commit(b_tfull + 8 * acc);  // accumulator ready for the epilogue
-                any = true;
-                if (++acc == 2) {
-                    acc = 0;
-                    acc_phase ^= 1;
-                }
             }
-            if (!ok) {
-                s_abort = 1;
-                atomicExch(g.status, (int)TRI_ETIMEOUT);
+            if (!ok) break;
+            if (leader) umma_commit(b_tfull + 8 * acc);  // accumulator ready for the epilogue
+            if (++acc == 2) {
+                acc = 0;
+                acc_phase ^= 1;
             }
-            // all issued MMAs complete before TMEM is released
-            umma_commit(b_done);
-            mbar_wait(b_done, 0, nullptr);
-            (void)any;
         }
+        if (!ok && leader) {
+            s_abort = 1;
+            atomicExch(g.status, (int)TRI_ETIMEOUT);
+        }
+        // all issued MMAs complete before TMEM is released
+        if (leader) umma_commit(b_done);
+        warp_wait(b_done, 0, nullptr);
     } else {
-        // ------------------------------------------------ epilogue (warps 2..5)
-        const uint32_t q = warp & 3;  // TMEM lane quarter this warp may access
-        float *stg = epi + (warp - 2) * EPI_STAGE_FLOATS;
-        uint32_t acc = 0, acc_phase = 0;
-        for (uint64_t t = t0; t < t1; ++t) {
+        // ------------------------------------------------ epilogue (warps 2..17)
+        // The accumulator holds the tile transposed: TMEM lane = output column
+        // j, TMEM column = output row i.  Warp e = warp - 2 reads lane quarter
+        // q = warp % 4 (the quarter a warp may access), so each thread owns one
+        // column j, and takes the 16-row chunks c = grp, grp+4 (grp = e / 4)
+        // of the tile's 8.  For every row the warp's 32 lanes hold 32
+        // consecutive entries of that packed row: one coalesced 128-byte
+        // store per row, straight from registers.  The next chunk's TMEM load
+        // is in flight while the current one is processed; the next tile's
+        // norms are fetched while the current tile is stored.
+        const uint32_t e = warp - 2, q = warp & 3, grp = e >> 2;
+        constexpr int NCH = TILE / EPI_ROWS / 4;  // chunks per warp and tile
+        float *snorm = epi + e * NORM_FLOATS;     // row norms of the tile, two buffers
+        const float tau = g.tau;
+        auto next_valid = [&](uint64_t t) {
+            uint32_t a, b;
+            while (t < t1 && !tile_of<MAP>(t, g.m, a, b)) ++t;
+            return t;
+        };
+        // next tile's norms: lane l holds the norms of rows l of chunks
+        // grp, grp+4 (16 each) and of its own column
+        float pfr = 0.0f, pfj = 0.0f;
+        auto prefetch = [&](uint64_t t) {
+            uint32_t a, b;
+            tile_of<MAP>(t, g.m, a, b);
+            const uint32_t ii = a * TILE + (grp + 4 * (lane >> 4)) * EPI_ROWS + (lane & 15);
+            const uint32_t jj = b * TILE + q * 32 + lane;
+            pfr = ii < g.n ? __ldg(g.norms + ii) : 0.0f;
+            pfj = jj < g.n ? __ldg(g.norms + jj) : 0.0f;
+        };
+        uint32_t acc = 0, acc_phase = 0, nbuf = 0;
+        uint64_t t = next_valid(t0);
+        if (t < t1) prefetch(t);
+        while (t < t1) {
             uint32_t bi, bj;
-            if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
-            int ready = 0;
-            if (lane == 0) ready = mbar_wait(b_tfull + 8 * acc, acc_phase, &s_abort) ? 1 : 0;
-            ready = __shfl_sync(0xffffffffu, ready, 0);  // warp-uniform, and the warp reconverges
-            if (!ready) {
+            tile_of<MAP>(t, g.m, bi, bj);
+            float *rn = snorm + nbuf * TILE;  // this tile's row norms: [chunk u][16]
+            rn[lane] = pfr;
+            const float nj = pfj;
+            __syncwarp();
+            const uint64_t tn = next_valid(t + 1);
+            if (tn < t1) prefetch(tn);
+            if (!warp_wait(b_tfull + 8 * acc, acc_phase, &s_abort)) {
                 if (lane == 0) {
                     s_abort = 1;
                     atomicExch(g.status, (int)TRI_ETIMEOUT);
@@ -426,39 +508,70 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t row0 = bi * TILE + q * 32;      // this warp's first row
-            const uint32_t i = row0 + lane;                 // this thread's row
-            const float ni = i < g.n ? __ldg(g.norms + i) : 0.0f;
-            for (int c = 0; c < TILE / 32; ++c) {
-                const uint32_t col0 = bj * TILE + c * 32;
-                float v[32];
-                tmem_ld32(tmem + ((q * 32) << 16) + acc * TILE + c * 32, v);
-                const uint32_t jl = col0 + lane;
-                const float nj_l = jl < g.n ? __ldg(g.norms + jl) : 0.0f;
+            const uint32_t j = bj * TILE + q * 32 + lane;  // this thread's column
+            // interior tiles need no masks: below the diagonal and inside n
+            const bool interior = bi != bj && (bi + 1) * TILE <= g.n;
+            const uint32_t taddr = tmem + ((q * 32) << 16) + acc * TILE;
+            uint32_t raw[2][EPI_ROWS];
+            tmem_ld16(taddr + grp * EPI_ROWS, raw[0]);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const float nj = __shfl_sync(0xffffffffu, nj_l, k);
-                    const uint32_t j = col0 + k;
-                    const float s = ni + nj;
-                    const float d2 = fmaf(-2.0f, v[k], s);
-                    float dist = sqrtf(fmaxf(d2, 0.0f));
-                    if (i == j) dist = 0.0f;
-                    if (i < g.n && j < i && d2 < g.tau * s) {
-                        const unsigned long long slot = atomicAdd(g.flag_count, 1ull);
-                        if (slot < g.flag_cap) g.flag_list[slot] = ((unsigned long long)i << 32) | j;
+            for (int u = 0; u < NCH; ++u) {
+                uint32_t(&cur)[EPI_ROWS] = raw[u & 1];
+                tmem_wait16(cur);
+                if (u + 1 < NCH) tmem_ld16(taddr + (grp + 4 * (u + 1)) * EPI_ROWS, raw[(u + 1) & 1]);
+                const uint32_t i0 = bi * TILE + (grp + 4 * u) * EPI_ROWS;  // first row of the chunk
+                float ni[EPI_ROWS];
+#pragma unroll
+                for (int k = 0; k < EPI_ROWS; k += 4) {
+                    const float4 v4 = *reinterpret_cast<const float4 *>(rn + u * EPI_ROWS + k);
+                    ni[k] = v4.x;
+                    ni[k + 1] = v4.y;
+                    ni[k + 2] = v4.z;
+                    ni[k + 3] = v4.w;
+                }
+                // fast path: d = d2 * rsqrt(d2); one test per chunk for a pair
+                // with d2 <= tau (|x_i|^2 + |x_j|^2) (cancellation, the
+                // diagonal, or padding)
+                float dv[EPI_ROWS], d2v[EPI_ROWS];
+                float worst = 1.0f;
+#pragma unroll
+                for (int k = 0; k < EPI_ROWS; ++k) {
+                    const float s = ni[k] + nj;
+                    const float d2 = fmaf(-2.0f, __uint_as_float(cur[k]), s);
+                    d2v[k] = d2;
+                    worst = fminf(worst, fmaf(-tau, s, d2));
+                    dv[k] = d2 * rsqrt_approx(d2);
+                }
+                if (worst <= 0.0f) {
+#pragma unroll
+                    for (int k = 0; k < EPI_ROWS; ++k) {
+                        const float d2 = d2v[k];
+                        if (d2 <= tau * (ni[k] + nj)) {
+                            const uint32_t i = i0 + k;
+                            if (i < g.n && j < i) {
+                                const unsigned long long slot = atomicAdd(g.flag_count, 1ull);
+                                if (slot < g.flag_cap) g.flag_list[slot] = ((unsigned long long)i << 32) | j;
+                            }
+                            // provisional value (flagged pairs are recomputed; the diagonal is exact 0)
+                            dv[k] = (i == j || d2 <= 0.0f) ? 0.0f : d2 * rsqrt_approx(d2);
+                        }
                     }
-                    stg[lane * 33 + k] = dist;
                 }
-                __syncwarp();
-                uint64_t tri_row = T2(row0);
-                for (int r = 0; r < 32; ++r) {
-                    const uint32_t ir = row0 + r;
-                    if (ir >= g.n) break;
-                    const uint32_t j = col0 + lane;
-                    if (j <= ir) __stcs(g.out + tri_row + j, stg[r * 33 + lane]);
-                    tri_row += ir + 1;
+                float *row = g.out + T2(i0) + j;  // row i0, column j
+                if (interior) {
+#pragma unroll
+                    for (int k = 0; k < EPI_ROWS; ++k) {
+                        __stcs(row, dv[k]);
+                        row += i0 + k + 1;  // T2(i + 1) - T2(i)
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < EPI_ROWS; ++k) {
+                        const uint32_t i = i0 + k;
+                        if (i < g.n && j <= i) __stcs(row, dv[k]);
+                        row += i + 1;
+                    }
                 }
-                __syncwarp();
             }
             tc_fence_before();
             if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
@@ -466,6 +579,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 acc = 0;
                 acc_phase ^= 1;
             }
+            nbuf ^= 1;
+            t = tn;
         }
     }
     tc_fence_before();
@@ -555,8 +670,8 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.P = prec == TRI_BF16X6 ? 3 : 2;
     p.dp = (d + KCH - 1) / KCH * KCH;
     p.nkc = p.dp / KCH;
-    const size_t fixed = 1024 /*align*/ + 4 * EPI_STAGE_FLOATS * 4 + 8 * (7 + 2 * 8);
-    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = (size_t)p.P * CHUNK_BYTES;
+    const size_t fixed = 1024 /*align*/ + NEPI * NORM_FLOATS * 4 + 8 * (7 + 2 * 8);
+    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
     p.stages = (uint32_t)std::min<size_t>(8, (SMEM_LIMIT - fixed - a) / st);
     p.smem = fixed + a + p.stages * st;

@@ -45,6 +45,9 @@ _SIGS = {
     "tri_lambda_verify": ([_i32, _i32, _u64, _u64, _vp, _vp], _i32),
     "tri_edm": ([_vp, _u32, _u32, _vp, _i32, _u32, _u32, _i32, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
+    "tri_edm_prepare": ([_vp, _u32, _u32, _i32, _vp, _sz, _vp], _i32),
+    "tri_edm_gram": ([_u32, _u32, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
+    "tri_edm_fixup": ([_vp, _u32, _u32, _vp, _i32, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_batched": ([_vp, _vp, _vp, _u32, _u32, _vp, _vp, _u32, _u32, _vp, _sz, _vp], _i32),
     "tri_edm_batched_workspace_size": ([_u32, _szp], _i32),
     "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
@@ -129,6 +132,27 @@ def tri_edm(x, out, map: int = MAP_LAMBDA, rho: int = 16, reg: int = 0, prec: in
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("tri_edm", _lib.tri_edm(_ptr(x), n, d, _ptr(out), map, rho, reg, prec, _ptr(workspace), ws_bytes,
                                    _ptr(n_flagged), _stream(stream)))
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size() if t is not None else 0
+
+
+def tri_edm_prepare(x, prec: int, workspace, stream=None) -> None:
+    n, d = x.shape
+    _check("tri_edm_prepare", _lib.tri_edm_prepare(_ptr(x), n, d, prec, _ptr(workspace), _nbytes(workspace),
+                                                   _stream(stream)))
+
+
+def tri_edm_gram(n: int, d: int, out, map: int, prec: int, workspace, stream=None) -> None:
+    _check("tri_edm_gram", _lib.tri_edm_gram(n, d, _ptr(out), map, prec, _ptr(workspace), _nbytes(workspace),
+                                             _stream(stream)))
+
+
+def tri_edm_fixup(x, out, prec: int, workspace, n_flagged=None, stream=None) -> None:
+    n, d = x.shape
+    _check("tri_edm_fixup", _lib.tri_edm_fixup(_ptr(x), n, d, _ptr(out), prec, _ptr(workspace),
+                                               _nbytes(workspace), _ptr(n_flagged), _stream(stream)))
 
 
 def tri_edm_batched_workspace_size(count: int) -> int:
