@@ -17,8 +17,8 @@
 // pair tiles taken in lambda order (Eq. eq_gmap) as one contiguous run of
 // tile numbers per CTA, so consecutive tiles share their row block and the
 // CTA keeps that row block's planes (A) resident in shared memory while TMA
-// streams the column blocks (B) through a ring of 16 KB stages, one per
-// (64-wide K chunk, plane).  Warp 0 issues TMA,
+// streams the column blocks (B) through a ring of stages, one per 64-wide K
+// chunk (all planes).  Warp 0 issues TMA,
 // warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator (with the
 // column block as the M operand, so TMEM lanes are output columns), warps
 // 2-17 read TMEM back, form the distances, flag cancellations and store each
@@ -274,11 +274,6 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 __device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr) { return (addr >> 4) | (1u << 16); }
 constexpr uint32_t kDescHi = (1024u >> 4) | (1u << 14) | (2u << 29);  // SBO, version, 128-byte swizzle
 
-__device__ __forceinline__ void umma_bf16_lo(uint32_t tmem_d, uint32_t a_lo, uint32_t b_lo, uint32_t accumulate)
-{
-    const uint64_t a = ((uint64_t)kDescHi << 32) | a_lo, b = ((uint64_t)kDescHi << 32) | b_lo;
-    umma_bf16(tmem_d, a, b, accumulate);
-}
 
 template <int MAP, int P>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -290,9 +285,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;
-    const uint32_t stage_bytes = CHUNK_BYTES;
+    const uint32_t stage_bytes = (uint32_t)P * CHUNK_BYTES;
     const uint32_t sA = base;                                  // [kc][p] chunks
-    const uint32_t sB = base + a_bytes;                        // [stage] chunks, one (K chunk, plane) each
+    const uint32_t sB = base + a_bytes;                        // [stage][p] chunks: one K chunk, all planes
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(epi + NEPI * NORM_FLOATS);
     // barriers: fullA, freeA, done, tmem_full[2], tmem_empty[2], fullB[stages], emptyB[stages]
@@ -334,42 +329,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint64_t t0 = (uint64_t)blockIdx.x * per;
     const uint64_t t1 = t0 + per < g.ntiles ? t0 + per : g.ntiles;
 
-    // The TMA and MMA roles run as whole warps: every lane walks the same
-    // loop (so tile, stage and descriptor values stay warp-uniform) and one
-    // lane issues the copies, MMAs and commits.
-    const bool leader = lane == 0;
+    // The TMA and MMA roles run on lane 0 of their warps.  Between two MMAs
+    // the issuing thread does nothing but add descriptor offsets: a
+    // 128x128x16 MMA takes about 68 cycles, and any longer gap in the issue
+    // stream leaves the tensor pipe idle.  Each stage holds one 64-wide K
+    // chunk of all planes of the column block, so the MMA thread waits once
+    // per 4 P(P+1)/2 MMAs.
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
-        if (leader) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
-        uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, loads = 0;
-        bool ok = true;
-        for (uint64_t t = t0; t < t1 && ok; ++t) {
-            uint32_t bi, bj;
-            if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
-            if (bi != a_row) {
-                if (a_loads > 0 && !warp_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
-                    ok = false;
-                    break;
-                }
-                if (leader) {
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, loads = 0;
+            bool ok = true;
+            for (uint64_t t = t0; t < t1 && ok; ++t) {
+                uint32_t bi, bj;
+                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+                if (bi != a_row) {
+                    if (a_loads > 0 && !mbar_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
                     mbar_expect_tx(b_fullA, a_bytes);
                     for (uint32_t kc = 0; kc < g.nkc; ++kc)
                         for (int p = 0; p < P; ++p)
                             tma_load_3d(sA + (kc * P + p) * CHUNK_BYTES, &tmap, b_fullA, kc * KCH, bi * TILE, p);
+                    ++a_loads;
+                    a_row = bi;
                 }
-                ++a_loads;
-                a_row = bi;
-            }
-            for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
-                for (int p = 0; p < P; ++p) {  // one stage per (K chunk, plane) of the column block
-                    if (!warp_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
+                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
+                    if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
                         ok = false;
                         break;
                     }
-                    if (leader) {
-                        mbar_expect_tx(b_fullB + 8 * stage, CHUNK_BYTES);
-                        tma_load_3d(sB + stage * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH, bj * TILE, p);
-                    }
+                    mbar_expect_tx(b_fullB + 8 * stage, stage_bytes);
+                    for (int p = 0; p < P; ++p)
+                        tma_load_3d(sB + (stage * P + p) * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH,
+                                    bj * TILE, p);
                     ++loads;
                     if (++stage == g.stages) {
                         stage = 0;
@@ -377,99 +372,97 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
             }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(g.status, (int)TRI_ETIMEOUT);
+            }
+            // never leave a copy in flight: wait for the last load into every
+            // stage (load k went to stage k % stages, in phase k / stages)
+            for (uint32_t st = 0; st < g.stages && st < loads; ++st) {
+                const uint32_t last = loads - 1 - ((loads - 1 - st) % g.stages);
+                mbar_wait(b_fullB + 8 * st, (last / g.stages) & 1, nullptr);
+            }
+            if (a_loads) mbar_wait(b_fullA, (a_loads - 1) & 1, nullptr);
         }
-        if (!ok && leader) {
-            s_abort = 1;
-            atomicExch(g.status, (int)TRI_ETIMEOUT);
-        }
-        // never leave a copy in flight: wait for the last load into every
-        // stage (load k went to stage k % stages, in phase k / stages)
-        for (uint32_t st = 0; st < g.stages && st < loads; ++st) {
-            const uint32_t last = loads - 1 - ((loads - 1 - st) % g.stages);
-            warp_wait(b_fullB + 8 * st, (last / g.stages) & 1, nullptr);
-        }
-        if (a_loads) warp_wait(b_fullA, (a_loads - 1) & 1, nullptr);
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
-        uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, acc = 0, acc_phase = 0;
-        bool ok = true;
-        for (uint64_t t = t0; t < t1 && ok; ++t) {
-            uint32_t bi, bj;
-            if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
-            if (bi != a_row) {
-                if (a_loads > 0 && leader) umma_commit(b_freeA);  // old A is free once issued MMAs finish
-                if (!warp_wait(b_fullA, a_loads & 1, &s_abort)) {
+        if (lane == 0) {
+            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, acc = 0, acc_phase = 0;
+            bool ok = true;
+            const uint64_t a_desc0 = ((uint64_t)kDescHi << 32) | sdesc_lo(sA);
+            const uint64_t b_desc0 = ((uint64_t)kDescHi << 32) | sdesc_lo(sB);
+            constexpr uint32_t CH16 = CHUNK_BYTES >> 4;  // one 16 KB chunk in descriptor units
+            for (uint64_t t = t0; t < t1 && ok; ++t) {
+                uint32_t bi, bj;
+                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+                if (bi != a_row) {
+                    if (a_loads > 0) umma_commit(b_freeA);  // old A is free once issued MMAs finish
+                    if (!mbar_wait(b_fullA, a_loads & 1, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    ++a_loads;
+                    a_row = bi;
+                }
+                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort)) {
                     ok = false;
                     break;
                 }
-                ++a_loads;
-                a_row = bi;
-            }
-            if (!warp_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t d_tmem = tmem + acc * TILE;
-            uint32_t accumulate = 0;
-            for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
-                const uint32_t a_lo = sdesc_lo(sA + kc * P * CHUNK_BYTES);
-#pragma unroll
-                for (int pb = 0; pb < P; ++pb) {
-                    if (!warp_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + acc * TILE;
+                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
+                    if (!mbar_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t b_lo = sdesc_lo(sB + stage * CHUNK_BYTES);
-                    if (leader) {
+                    const uint64_t a_desc = a_desc0 + kc * P * CH16;
+                    const uint64_t b_desc = b_desc0 + stage * P * CH16;
 #pragma unroll
-                        for (int pa = 0; pa + pb < P; ++pa) {
+                    for (int pb = 0; pb < P; ++pb)
 #pragma unroll
-                            for (int kk = 0; kk < KCH / 16; ++kk) {
+                        for (int pa = 0; pa + pb < P; ++pa)
+#pragma unroll
+                            for (int kk = 0; kk < KCH / 16; ++kk)
                                 // the column tile is the M operand: TMEM lane = output column;
                                 // +2 per 16-element K step (32 bytes in 16-byte units)
-                                umma_bf16_lo(d_tmem, b_lo + 2 * kk, a_lo + pa * (CHUNK_BYTES >> 4) + 2 * kk,
-                                             accumulate);
-                                accumulate = 1;
-                            }
-                        }
-                        umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
-                    }
-                    accumulate = 1;
+                                umma_bf16(d_tmem, b_desc + pb * CH16 + 2 * kk, a_desc + pa * CH16 + 2 * kk,
+                                          (kc | pb | pa | kk) ? 1u : 0u);
+                    umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
                     if (++stage == g.stages) {
                         stage = 0;
                         b_phase ^= 1;
                     }
                 }
+                if (!ok) break;
+                umma_commit(b_tfull + 8 * acc);  // accumulator ready for the epilogue
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1;
+                }
             }
-            if (!ok) break;
-            if (leader) umma_commit(b_tfull + 8 * acc);  // accumulator ready for the epilogue
-            if (++acc == 2) {
-                acc = 0;
-                acc_phase ^= 1;
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(g.status, (int)TRI_ETIMEOUT);
             }
+            // all issued MMAs complete before TMEM is released
+            umma_commit(b_done);
+            mbar_wait(b_done, 0, nullptr);
         }
-        if (!ok && leader) {
-            s_abort = 1;
-            atomicExch(g.status, (int)TRI_ETIMEOUT);
-        }
-        // all issued MMAs complete before TMEM is released
-        if (leader) umma_commit(b_done);
-        warp_wait(b_done, 0, nullptr);
     } else {
         // ------------------------------------------------ epilogue (warps 2..17)
         // The accumulator holds the tile transposed: TMEM lane = output column
         // j, TMEM column = output row i.  Warp e = warp - 2 reads lane quarter
         // q = warp % 4 (the quarter a warp may access), so each thread owns one
-        // column j, and takes the 16-row chunks c = grp, grp+4 (grp = e / 4)
-        // of the tile's 8.  For every row the warp's 32 lanes hold 32
+        // column j, and takes the 16-row chunks c = grp + NG u (grp = e / 4,
+        // NG = NEPI / 4 warps per quarter) of the tile's 8.  For every row the warp's 32 lanes hold 32
         // consecutive entries of that packed row: one coalesced 128-byte
         // store per row, straight from registers.  The next chunk's TMEM load
         // is in flight while the current one is processed; the next tile's
         // norms are fetched while the current tile is stored.
+        constexpr int NG = NEPI / 4;                // warps per TMEM lane quarter
+        constexpr int NCH = TILE / EPI_ROWS / NG;   // 16-row chunks per warp and tile
         const uint32_t e = warp - 2, q = warp & 3, grp = e >> 2;
-        constexpr int NCH = TILE / EPI_ROWS / 4;  // chunks per warp and tile
         float *snorm = epi + e * NORM_FLOATS;     // row norms of the tile, two buffers
         const float tau = g.tau;
         auto next_valid = [&](uint64_t t) {
@@ -477,15 +470,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             while (t < t1 && !tile_of<MAP>(t, g.m, a, b)) ++t;
             return t;
         };
-        // next tile's norms: lane l holds the norms of rows l of chunks
-        // grp, grp+4 (16 each) and of its own column
-        float pfr = 0.0f, pfj = 0.0f;
+        // next tile's norms: lane l holds the norms of row l % 16 of chunks
+        // u = 2v + l / 16 (16 rows each) and of its own column
+        float pfr[NCH / 2], pfj = 0.0f;
         auto prefetch = [&](uint64_t t) {
             uint32_t a, b;
             tile_of<MAP>(t, g.m, a, b);
-            const uint32_t ii = a * TILE + (grp + 4 * (lane >> 4)) * EPI_ROWS + (lane & 15);
+#pragma unroll
+            for (int v = 0; v < NCH / 2; ++v) {
+                const uint32_t u = 2 * v + (lane >> 4);
+                const uint32_t ii = a * TILE + (grp + NG * u) * EPI_ROWS + (lane & 15);
+                pfr[v] = ii < g.n ? __ldg(g.norms + ii) : 0.0f;
+            }
             const uint32_t jj = b * TILE + q * 32 + lane;
-            pfr = ii < g.n ? __ldg(g.norms + ii) : 0.0f;
             pfj = jj < g.n ? __ldg(g.norms + jj) : 0.0f;
         };
         uint32_t acc = 0, acc_phase = 0, nbuf = 0;
@@ -495,7 +492,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint32_t bi, bj;
             tile_of<MAP>(t, g.m, bi, bj);
             float *rn = snorm + nbuf * TILE;  // this tile's row norms: [chunk u][16]
-            rn[lane] = pfr;
+#pragma unroll
+            for (int v = 0; v < NCH / 2; ++v) rn[32 * v + lane] = pfr[v];
             const float nj = pfj;
             __syncwarp();
             const uint64_t tn = next_valid(t + 1);
@@ -518,8 +516,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int u = 0; u < NCH; ++u) {
                 uint32_t(&cur)[EPI_ROWS] = raw[u & 1];
                 tmem_wait16(cur);
-                if (u + 1 < NCH) tmem_ld16(taddr + (grp + 4 * (u + 1)) * EPI_ROWS, raw[(u + 1) & 1]);
-                const uint32_t i0 = bi * TILE + (grp + 4 * u) * EPI_ROWS;  // first row of the chunk
+                if (u + 1 < NCH) tmem_ld16(taddr + (grp + NG * (u + 1)) * EPI_ROWS, raw[(u + 1) & 1]);
+                const uint32_t i0 = bi * TILE + (grp + NG * u) * EPI_ROWS;  // first row of the chunk
                 float ni[EPI_ROWS];
 #pragma unroll
                 for (int k = 0; k < EPI_ROWS; k += 4) {
@@ -671,7 +669,7 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.dp = (d + KCH - 1) / KCH * KCH;
     p.nkc = p.dp / KCH;
     const size_t fixed = 1024 /*align*/ + NEPI * NORM_FLOATS * 4 + 8 * (7 + 2 * 8);
-    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;
+    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = (size_t)p.P * CHUNK_BYTES;
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
     p.stages = (uint32_t)std::min<size_t>(8, (SMEM_LIMIT - fixed - a) / st);
     p.smem = fixed + a + p.stages * st;
