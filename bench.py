@@ -39,6 +39,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 NUM_SMS = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one Gram-kernel launch, from the ncu capture
+# summarised in profiles/gram_kernel_lambda_bf16x6_n65536_d128.md (taken at
+# N = 16384 and scaled by the number of pairs).  Keyed by (prec, n, d); a
+# kernel change makes the figure stale, and it is then removed.
+NCU_TRAFFIC = {("bf16x6", 65536, 128): 8.00e9}
 
 
 def load_peaks():
@@ -294,13 +299,14 @@ def main():
         hbm = nbytes / t_gram / 1e9
         tiles = (-(-N_PTS // 128)) * (-(-N_PTS // 128) + 1) // 2
         tflop = 2.0 * dp * nprod * tiles * 128 * 128 / t_gram / 1e12
+        traffic = NCU_TRAFFIC.get((args.prec, N_PTS, D_FEAT))
         roof_hbm = {"bound": "hbm", "kernel": f"gram_kernel<lambda,{planes}>", "achieved": hbm,
                     "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": hbm / float(peaks["hbm_gbs"]),
-                    "traffic": None, "algorithmic_bytes": nbytes,
+                    "traffic": traffic, "algorithmic_bytes": nbytes,
                     "peak_source": f"hbm_gbs of {peak_src}"}
         roof_tc = {"bound": "tensor", "kernel": f"gram_kernel<lambda,{planes}>", "achieved": tflop,
                    "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
-                   "frac": tflop / float(peaks["bf16_tflops"]), "traffic": None,
+                   "frac": tflop / float(peaks["bf16_tflops"]), "traffic": traffic,
                    "flops": 2.0 * dp * nprod * tiles * 128 * 128,
                    "peak_source": f"bf16_tflops (burst) of {peak_src}"}
         roof, roof_alt = (roof_hbm, roof_tc) if roof_hbm["frac"] >= roof_tc["frac"] else (roof_tc, roof_hbm)
