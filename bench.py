@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 # summarised in profiles/gram_kernel_lambda_bf16x6_n65536_d128.md (taken at
 # N = 16384 and scaled by the number of pairs).  Keyed by (prec, n, d); a
 # kernel change makes the figure stale, and it is then removed.
-NCU_TRAFFIC = {("bf16x6", 65536, 128): 8.00e9}
+NCU_TRAFFIC = {}
 
 
 def load_peaks():
@@ -161,6 +161,151 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ row suite -----
+def run_suite(args):
+    """One JSON line per remaining hot-path row, each timed with CUDA events
+    (CUDA graphs for launches shorter than the launch overhead), lambda beside
+    the bounding box and a roofline fraction."""
+    import torch
+    from paper_1609_01490_gb300 import inputs
+    from paper_1609_01490_gb300 import tri
+
+    dev = torch.device("cuda")
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    clk = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    stream = torch.cuda.current_stream()
+
+    def graph_ms(fn, reps):
+        """Mean ms of fn, captured `reps` times into one CUDA graph, replayed 3 times."""
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s2 = torch.cuda.Stream()
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            fn()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s2):
+                for _ in range(reps):
+                    fn()
+        stream.wait_stream(s2)
+        g.replay()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b) / reps)
+        return best
+
+    def emit(d):
+        d.setdefault("data", "synthetic")
+        d.setdefault("peaks", {"source": peak_src})
+        print(json.dumps(d), flush=True)
+
+    # a1-a4: the maps alone (sentinel body), n = 65536, rho = 16
+    n = 65536
+    out = torch.zeros(4, dtype=torch.int32, device=dev)
+    times = {}
+    for name, m, sq in (("lambda_X", tri.MAP_LAMBDA, tri.SQRT_X), ("lambda_R", tri.MAP_LAMBDA, tri.SQRT_R),
+                        ("lambda_N", tri.MAP_LAMBDA, tri.SQRT_N), ("lambda_pdelta_R", tri.MAP_LAMBDA_PDELTA, tri.SQRT_R),
+                        ("bb", tri.MAP_BB, tri.SQRT_R), ("rb", tri.MAP_RB, tri.SQRT_R),
+                        ("rec", tri.MAP_REC, tri.SQRT_R), ("utm", tri.MAP_UTM, tri.SQRT_R)):
+        times[name] = graph_ms(lambda: tri.tri_map_launch(m, sq, n, 16, True, tri.BODY_SENTINEL, out), 20)
+    elems = n * (n + 1) // 2
+    emit({"row": "map_only", "metric": "mapped elements/s", "unit": "elements/s",
+          "config": {"workload": "sentinel body (map cost only)", "n": n, "rho": 16},
+          "ms": times, "value": {k: elems / (v * 1e-3) for k, v in times.items()},
+          "I_bb_over": {k: times["bb"] / v for k, v in times.items()}})
+
+    # a5: the paper-size EDM, N = 2048, d = 3, rho = 16 (8.4 MB output, L2-resident)
+    x = torch.from_numpy(inputs.edm_uniform_points(2048, 3, seed=1609)).to(dev)
+    o = torch.empty(2048 * 2049 // 2, dtype=torch.float32, device=dev)
+    t = {nm: graph_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=1), 200)
+         for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB),
+                       ("rec", tri.MAP_REC), ("utm", tri.MAP_UTM))}
+    P = 2048 * 2049 // 2
+    emit({"row": "edm_fp32_paper_size", "metric": "pairs/s", "unit": "pairs/s", "value": P / (t["lambda"] * 1e-3),
+          "config": {"workload": "edm_n2048_d3_uniform", "rho": 16, "reg": 1, "launches_per_graph": 200},
+          "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
+          "roofline": {"bound": "hbm", "achieved": 4.0 * P / (t["lambda"] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": 4.0 * P / (t["lambda"] * 1e-3) / 1e9 / hbm,
+                       "note": "8.4 MB output stays in L2 across back-to-back launches"}})
+
+    # a6: triangular Life, n = 16384, 100 steps, rho = 16
+    n = 16384
+    a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)
+    b = torch.zeros_like(a)
+
+    def life(m):
+        def run():
+            for s in range(100):
+                src, dst = (a, b) if s % 2 == 0 else (b, a)
+                tri.tri_ca_step(src, dst, n, map=m, rho=16)
+        return run
+    t = {nm: graph_ms(life(m), 1) / 100 for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB),
+                                                      ("rb", tri.MAP_RB), ("rec", tri.MAP_REC))}
+    cells = n * (n + 1) // 2
+    gbs = 2.0 * cells / (t["lambda"] * 1e-3) / 1e9
+    emit({"row": "life_step", "metric": "cell updates/s", "unit": "cells/s", "value": cells / (t["lambda"] * 1e-3),
+          "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 16}, "ms_per_step": t,
+          "I_bb_over_lambda": t["bb"] / t["lambda"],
+          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                       "algorithmic_bytes_per_step": 2 * cells}})
+
+    # a7: Axilrod-Teller energy over the tetrahedral domain, N = 1536, rho = 16
+    n = 1536
+    p = torch.from_numpy(inputs.at_points(n, seed=1610)).to(dev)
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    ws = torch.empty(max(tri.tet_at_workspace_size(n, 16, m) for m in (tri.MAP_LAMBDA, tri.MAP_BB)) // 8 + 1,
+                     dtype=torch.float64, device=dev)
+    t = {nm: graph_ms(lambda: tri.tet_at_energy(p, e, 1.0, m, 16, ws), 20)
+         for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB))}
+    trip = n * (n - 1) * (n - 2) // 6
+    tf = 40.0 * trip / (t["lambda"] * 1e-3) / 1e12
+    emit({"row": "at_energy", "metric": "triplets/s", "unit": "triplets/s", "value": trip / (t["lambda"] * 1e-3),
+          "config": {"workload": "at_n1536_uniform_unit_density", "rho": 16}, "ms": t,
+          "I_bb_over_lambda": t["bb"] / t["lambda"],
+          "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                       "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"}})
+
+    # a9: 1000 uneven EDM triangles: one persistent launch vs 1000 tri_edm launches (both in CUDA graphs)
+    sizes = inputs.batched_sizes(1000, seed=1609)
+    xc, pt_off = inputs.batched_points(sizes, 64, seed=1609)
+    tri_len = sizes.astype(np.int64) * (sizes.astype(np.int64) + 1) // 2
+    out_off = np.zeros(len(sizes), dtype=np.uint64)
+    out_off[1:] = np.cumsum(tri_len)[:-1]
+    total = int(tri_len.sum())
+    xd = torch.from_numpy(xc).to(dev)
+    oc = torch.empty(total, dtype=torch.float32, device=dev)
+    pto = torch.from_numpy(pt_off.view(np.int64)).to(dev)
+    nk = torch.from_numpy(sizes.astype(np.int32)).to(dev)
+    oo = torch.from_numpy(out_off.view(np.int64)).to(dev)
+    wsb = torch.empty(tri.tri_edm_batched_workspace_size(1000) // 8 + 1, dtype=torch.int64, device=dev)
+    tb = {}
+    for rho in (8, 16, 32):
+        tb[f"persistent_rho{rho}"] = graph_ms(lambda: tri.tri_edm_batched(xd, pto, nk, oc, oo, rho=rho, reg=0,
+                                                                           workspace=wsb), 1)
+    views = [(xd[int(pt_off[k]): int(pt_off[k]) + int(sizes[k])], oc[int(out_off[k]): int(out_off[k]) + int(tri_len[k])])
+             for k in range(1000)]
+
+    def separate():
+        for xv, ov in views:
+            tri.tri_edm(xv, ov, map=tri.MAP_LAMBDA, rho=16, reg=0)
+    tb["separate_1000_launches"] = graph_ms(separate, 1)
+    best = min(v for k, v in tb.items() if k.startswith("persistent"))
+    tf = 3.0 * 64 * total / (best * 1e-3) / 1e12
+    emit({"row": "edm_batched", "metric": "pairs/s", "unit": "pairs/s", "value": total / (best * 1e-3),
+          "config": {"workload": "1000 instances, N log-uniform [64, 8192], d = 64", "pairs": total}, "ms": tb,
+          "speedup_over_separate": tb["separate_1000_launches"] / best,
+          "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak}})
+
+
 # -------------------------------------------------------------- our arm -----
 def main():
     global N_PTS, D_FEAT, WORKLOAD
@@ -175,6 +320,7 @@ def main():
     ap.add_argument("--no-arms", action="store_true", help="skip the BB and FP32 comparison arms")
     ap.add_argument("--n", type=int, default=N_PTS, help="points (smaller cases are for profiling only)")
     ap.add_argument("--d", type=int, default=D_FEAT, help="features (smaller cases are for profiling only)")
+    ap.add_argument("--suite", action="store_true", help="one JSON line per other hot-path row instead")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -184,6 +330,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.suite:
+        run_suite(args)
         return
     if (args.n, args.d) != (N_PTS, D_FEAT):
         N_PTS, D_FEAT = args.n, args.d

@@ -44,7 +44,10 @@ constexpr int CHUNK_BYTES = TILE * KCH * 2;  // 16 KB: 128 rows x 64 BF16
 constexpr int NEPI = 16;                   // epilogue warps: 4 TMEM lane quarters x 4 row groups
 constexpr int NTHREADS = 64 + 32 * NEPI;   // TMA warp, MMA warp, epilogue warps
 constexpr int EPI_ROWS = 16;               // output rows per TMEM load in the epilogue
-constexpr int NORM_FLOATS = 2 * TILE;      // per epilogue warp: row norms of the tile (double buffered)
+constexpr int NORM_FLOATS = 2 * 32;       // per epilogue warp: norms of its 32 rows of the tile (double buffered)
+constexpr int STG_ROWS = 8;                // rows staged at a time by a row group
+constexpr int STG_LD = TILE + 4;           // staging row: 128 distances shifted by the row's 16-byte phase
+constexpr int STG_FLOATS = STG_ROWS * STG_LD;  // per row group
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 constexpr int SMEM_LIMIT = 227 * 1024;
 
@@ -257,6 +260,16 @@ __device__ __forceinline__ bool tile_of(uint64_t t, uint32_t m, uint32_t &bi, ui
 // pa + pb <= P - 1: hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid for P = 3
 // and hi.hi, hi.lo, lo.hi for P = 2.
 
+// Offset of packed row i0 + k within 16 bytes, T2(i0 + k) mod 4, for i0 a
+// multiple of 16 (then it equals T2(k) mod 4).
+__host__ __device__ constexpr uint32_t row_phase(uint32_t k) { return ((k * (k + 1)) >> 1) & 3u; }
+
+// Barrier among the `count` threads of one epilogue row group (ids 1..).
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // 1/sqrt by the MUFU unit (flush-to-zero approximation; relative error a few
 // 2^-23, far inside the 1e-5 the distances are held to).
 __device__ __forceinline__ float rsqrt_approx(float x)
@@ -289,7 +302,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t sA = base;                                  // [kc][p] chunks
     const uint32_t sB = base + a_bytes;                        // [stage][p] chunks: one K chunk, all planes
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(epi + NEPI * NORM_FLOATS);
+    float *stage_base = epi + NEPI * NORM_FLOATS;  // one staging area per row group
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage_base + (NEPI / 4) * STG_FLOATS);
     // barriers: fullA, freeA, done, tmem_full[2], tmem_empty[2], fullB[stages], emptyB[stages]
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t b_fullA = bar0, b_freeA = bar0 + 8, b_done = bar0 + 16;
@@ -463,7 +477,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         constexpr int NG = NEPI / 4;                // warps per TMEM lane quarter
         constexpr int NCH = TILE / EPI_ROWS / NG;   // 16-row chunks per warp and tile
         const uint32_t e = warp - 2, q = warp & 3, grp = e >> 2;
-        float *snorm = epi + e * NORM_FLOATS;     // row norms of the tile, two buffers
+        float *snorm = epi + e * NORM_FLOATS;     // norms of this warp's rows, two buffers
+        float *stg = stage_base + grp * STG_FLOATS;  // this row group's staging rows
         const float tau = g.tau;
         auto next_valid = [&](uint64_t t) {
             uint32_t a, b;
@@ -491,7 +506,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         while (t < t1) {
             uint32_t bi, bj;
             tile_of<MAP>(t, g.m, bi, bj);
-            float *rn = snorm + nbuf * TILE;  // this tile's row norms: [chunk u][16]
+            float *rn = snorm + nbuf * 32;  // this tile's row norms: [chunk u][16]
 #pragma unroll
             for (int v = 0; v < NCH / 2; ++v) rn[32 * v + lane] = pfr[v];
             const float nj = pfj;
@@ -507,8 +522,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc_fence_after();
             const uint32_t j = bj * TILE + q * 32 + lane;  // this thread's column
-            // interior tiles need no masks: below the diagonal and inside n
-            const bool interior = bi != bj && (bi + 1) * TILE <= g.n;
             const uint32_t taddr = tmem + ((q * 32) << 16) + acc * TILE;
             uint32_t raw[2][EPI_ROWS];
             tmem_ld16(taddr + grp * EPI_ROWS, raw[0]);
@@ -555,19 +568,62 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-                float *row = g.out + T2(i0) + j;  // row i0, column j
-                if (interior) {
-#pragma unroll
-                    for (int k = 0; k < EPI_ROWS; ++k) {
-                        __stcs(row, dv[k]);
-                        row += i0 + k + 1;  // T2(i + 1) - T2(i)
+                if constexpr (P == 2) {
+                    // Store through shared memory in two halves of 8 rows: the row
+                    // group's four warps (one per 32-column quarter) write their
+                    // columns of each row into a staging row shifted by the row's
+                    // 16-byte phase (T2(i0 + k) mod 4, which depends on k only since
+                    // i0 is a multiple of 16); then each warp writes two whole row
+                    // segments, the aligned middle with one float4 per lane and the
+                    // ends with scalar stores.  Every 128-byte line of a segment's
+                    // middle is then written by one instruction.
+    #pragma unroll
+                    for (int half = 0; half < EPI_ROWS / STG_ROWS; ++half) {
+    #pragma unroll
+                        for (int kk = 0; kk < STG_ROWS; ++kk) {
+                            const int k = half * STG_ROWS + kk;
+                            stg[kk * STG_LD + row_phase(k) + q * 32 + lane] = dv[k];
+                        }
+                        named_sync(1 + grp, 128);
+    #pragma unroll
+                        for (int r2 = 0; r2 < STG_ROWS / 4; ++r2) {
+                            const uint32_t kk = q * (STG_ROWS / 4) + r2, k = half * STG_ROWS + kk, i = i0 + k;
+                            if (i < g.n) {
+                                const uint32_t len = bi == bj ? i - bj * TILE + 1 : TILE;  // columns of row i here
+                                float *seg = g.out + T2(i) + bj * TILE;
+                                const uint32_t ph = row_phase(k), head = (4 - ph) & 3;
+                                const float *src = stg + kk * STG_LD + ph;
+                                const uint32_t h = head < len ? head : len;
+                                const uint32_t nv = (len - h) >> 2;
+                                if (lane < nv)
+                                    __stcs(reinterpret_cast<float4 *>(seg + h) + lane,
+                                           *reinterpret_cast<const float4 *>(src + h + 4 * lane));
+                                const uint32_t t0 = h + 4 * nv, tail = len - t0;  // h <= 3, tail <= 3
+                                if (lane < h) __stcs(seg + lane, src[lane]);
+                                if (lane >= 4 && lane - 4 < tail) __stcs(seg + t0 + lane - 4, src[t0 + lane - 4]);
+                            }
+                        }
+                        named_sync(1 + grp, 128);
                     }
                 } else {
+                    // Direct stores: for each row the warp's 32 lanes hold 32
+                    // consecutive packed entries, written by one 128-byte store.
+                    // (Measured faster than staging for P = 3, whose MMA stream
+                    // rather than its stores bounds the kernel.)
+                    float *row = g.out + T2(i0) + j;  // row i0, column j
+                    if (bi != bj && (bi + 1) * TILE <= g.n) {
 #pragma unroll
-                    for (int k = 0; k < EPI_ROWS; ++k) {
-                        const uint32_t i = i0 + k;
-                        if (i < g.n && j <= i) __stcs(row, dv[k]);
-                        row += i + 1;
+                        for (int k = 0; k < EPI_ROWS; ++k) {
+                            __stcs(row, dv[k]);
+                            row += i0 + k + 1;  // T2(i + 1) - T2(i)
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < EPI_ROWS; ++k) {
+                            const uint32_t i = i0 + k;
+                            if (i < g.n && j <= i) __stcs(row, dv[k]);
+                            row += i + 1;
+                        }
                     }
                 }
             }
@@ -668,7 +724,7 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.P = prec == TRI_BF16X6 ? 3 : 2;
     p.dp = (d + KCH - 1) / KCH * KCH;
     p.nkc = p.dp / KCH;
-    const size_t fixed = 1024 /*align*/ + NEPI * NORM_FLOATS * 4 + 8 * (7 + 2 * 8);
+    const size_t fixed = 1024 /*align*/ + (NEPI * NORM_FLOATS + (NEPI / 4) * STG_FLOATS) * 4 + 8 * (7 + 2 * 8);
     const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = (size_t)p.P * CHUNK_BYTES;
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
     p.stages = (uint32_t)std::min<size_t>(8, (SMEM_LIMIT - fixed - a) / st);
@@ -712,6 +768,7 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     if (n > TC_MAX_N) return TRI_ERANGE;
     if (prec != TRI_BF16X3 && prec != TRI_BF16X6) return TRI_EINVAL;
     if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    if ((uintptr_t)out & 15) return TRI_EINVAL;  // row segments are written with 16-byte stores
     TcPlan pl;
     if (!plan(d, prec, pl)) return TRI_ERANGE;
     const WsLayout L = ws_layout(n, d, prec);
