@@ -237,6 +237,24 @@ def run_suite(args):
                        "frac": 4.0 * P / (t["lambda"] * 1e-3) / 1e9 / hbm,
                        "note": "8.4 MB output stays in L2 across back-to-back launches"}})
 
+    # a2/a5 at scale: N = 65536, d = 3 (store-bound, 8.6 GB of output) with the
+    # paper's block shape (one pair per thread, rho = 16) and with 4 x 4 pairs per thread
+    x = torch.from_numpy(inputs.edm_uniform_points(65536, 3, seed=1609)).to(dev)
+    o = torch.empty(65536 * 65537 // 2, dtype=torch.float32, device=dev)
+    P = 65536 * 65537 // 2
+    for reg in (1, 4):
+        t = {nm: graph_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=reg), 3)
+             for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB),
+                           ("rec", tri.MAP_REC))}
+        gbs = 4.0 * P / (t["lambda"] * 1e-3) / 1e9
+        emit({"row": f"edm_fp32_n65536_d3_reg{reg}", "metric": "pairs/s", "unit": "pairs/s",
+              "value": P / (t["lambda"] * 1e-3),
+              "config": {"workload": "edm_n65536_d3_uniform", "rho": 16, "reg": reg,
+                         "pairs_per_thread": reg * reg}, "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
+              "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}})
+    del x, o
+    torch.cuda.empty_cache()
+
     # a6: triangular Life, n = 16384, 100 steps, rho = 16
     n = 16384
     a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)

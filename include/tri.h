@@ -136,7 +136,7 @@ TRI_API int tri_lambda_verify(int sqrt_kind, int with_diag, uint64_t w_begin, ui
  *   out[i(i+1)/2 + j] = sqrt(sum_k (x[i][k] - x[j][k])^2), the diagonal 0.
  *   x (device, FP32) row-major [n][d]; out (device, FP32) n(n+1)/2 entries.
  *   prec = TRI_FP32: blocks of rho x rho threads, each thread reg x reg pairs
- *   (reg in {1, 2, 4}; 0 picks 1 for d <= 8, else 4); each block covers an
+ *   (reg in {1, 2, 4}; 0 picks 4); each block covers an
  *   S x S pair tile, S = rho*reg, placed by `map` (any tri_map).  No workspace.
  *   prec = TRI_BF16X3 / TRI_BF16X6: 128 x 128 pair tiles on tcgen05 tensor
  *   cores, placed by TRI_MAP_LAMBDA or TRI_MAP_BB; rho and reg are ignored;

@@ -10,7 +10,7 @@ against (``selector.py``).
 
 Kernels and their candidate maps:
   edm: lambda, lambda on P_Delta, BB, RB, REC, UTM (Section 4.2), FP32 direct
-       differences, reg = 1 for d <= 8 else 4
+       differences, 4 x 4 pairs per thread (reg = 4)
   ca:  lambda, lambda on P_Delta, BB, RB, REC (one Life step)
   at:  tetrahedral lambda, BB (Axilrod-Teller energy)
 REC is skipped where the block count is not a power of two.
@@ -52,7 +52,7 @@ def cand_name(map_id: int, rho: int) -> str:
 def applicable(kernel: str, map_id: int, n: int, rho: int, d: int = 1) -> bool:
     """Whether a candidate can run at this size (REC needs 2^k block rows)."""
     if map_id == tri.MAP_REC:
-        side = {"edm": rho * (1 if d <= 8 else 4), "ca": 4 * rho, "at": rho}[kernel]
+        side = {"edm": 4 * rho, "ca": 4 * rho, "at": rho}[kernel]
         m = -(-n // side)
         return m & (m - 1) == 0
     return True

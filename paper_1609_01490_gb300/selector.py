@@ -28,7 +28,7 @@ H1 = H2 = 64
 
 
 def _tile_side(kernel: str, rho: int, d: int) -> int:
-    return {"edm": rho * (1 if d <= 8 else 4), "ca": 4 * rho, "at": rho}[kernel]
+    return {"edm": 4 * rho, "ca": 4 * rho, "at": rho}[kernel]
 
 
 def _blocks(kernel: str, n: int, d: int, map_id: int, rho: int) -> float:

@@ -24,9 +24,9 @@ def test_autotune_small_live(tmp_path, monkeypatch):
         assert len(res) == ncand and all(v > 0 for v in res.values())
         m, r, ms = autotune.best(kernel, n, d)
         assert ms == min(res.values()) and autotune.cand_name(m, r) in res
-    # REC is skipped where the block count is not a power of two (1000 / 16 -> 63 blocks)
-    res = autotune.tune("edm", 1000, 3, reps=1, use_cache=False)
-    assert not any(k.startswith("rec/") for k in res if k.endswith("/16"))
+    # REC is skipped where the block count is not a power of two (1100 points / 64 -> 18 blocks)
+    res = autotune.tune("edm", 1100, 3, reps=1, use_cache=False)
+    assert not any(k.startswith("rec/") for k in res)
     cache = json.load(open(tmp_path / "cache.json"))
     assert len(cache) == 3
 

@@ -25,10 +25,11 @@ def test_features_and_blocks(sel):
     f = sel.features("edm", 2048, 3, tri.MAP_LAMBDA, 16)
     assert f.shape == (sel.NFEAT,) and np.all(np.isfinite(f))
     assert f[0] == 11 and f[2] == 4 and f[4] == 1 and f[7] == 1
-    # launched blocks: lambda m(m+1)/2, BB m^2, RB m * (m/2 + 1) for even m (Section 3.1, 4.2)
-    assert sel._blocks("edm", 2048, 3, tri.MAP_LAMBDA, 16) == 128 * 129 / 2
-    assert sel._blocks("edm", 2048, 3, tri.MAP_BB, 16) == 128 * 128
-    assert sel._blocks("edm", 2048, 3, tri.MAP_RB, 16) == 128 * 65
+    # launched blocks (tiles of 4 rho = 64 points): lambda m(m+1)/2, BB m^2, RB m (m/2 + 1) for
+    # even m (Section 3.1, 4.2)
+    assert sel._blocks("edm", 2048, 3, tri.MAP_LAMBDA, 16) == 32 * 33 / 2
+    assert sel._blocks("edm", 2048, 3, tri.MAP_BB, 16) == 32 * 32
+    assert sel._blocks("edm", 2048, 3, tri.MAP_RB, 16) == 32 * 17
     assert sel._blocks("at", 256, 3, tri.MAP_LAMBDA, 16) == 16 * 17 * 18 / 6
     assert math.isclose(sel._blocks("edm", 2048, 3, tri.MAP_UTM, 16), 2049 * 2048 / 2 / 256)
 
@@ -36,8 +37,10 @@ def test_features_and_blocks(sel):
 def test_candidates(sel):
     from paper_1609_01490_gb300 import tri
     assert len(sel.candidates("edm", 2048, 3)) == 18
-    # REC only where the block count is a power of two: 1000 points give 125, 63 and 32 blocks
-    assert len(sel.candidates("edm", 1000, 3)) == 16
+    # REC only where the block count is a power of two: 1000 points in tiles of 32, 64 and 128
+    # give 32, 16 and 8 block rows (all powers of two); 1100 points give 35, 18 and 9 (none)
+    assert len(sel.candidates("edm", 1000, 3)) == 18
+    assert len(sel.candidates("edm", 1100, 3)) == 15
     assert len(sel.candidates("at", 300, 3)) == 6
     assert all(m in (tri.MAP_LAMBDA, tri.MAP_BB) for m, _ in sel.candidates("at", 300, 3))
 
