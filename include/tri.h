@@ -161,8 +161,9 @@ TRI_API int tri_edm_workspace_size(uint32_t n, uint32_t d, int prec, size_t *byt
  * their own (same stream, in this order) to time them or to reuse prepared
  * operands.  workspace: tri_edm_workspace_size bytes, 256-byte aligned.
  * Tensor-core limits: n <= 92681 (packed triangle below 2^32 entries),
- * d <= 128 for BF16X6 and d <= 256 for BF16X3 (the split planes of one row
- * block stay resident in shared memory); larger sizes give TRI_ERANGE.
+ * d <= 192 for BF16X6 and d <= 320 for BF16X3 (the split planes of one row
+ * block stay resident in shared memory beside at least two 16 KB operand
+ * stages); larger sizes give TRI_ERANGE.
  *
  *   tri_edm_prepare: clears the workspace header, then writes the FP32 row
  *     norms |x_i|^2 (summed in FP64) and the BF16 split planes (hi, lo or hi,

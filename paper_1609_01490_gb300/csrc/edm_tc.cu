@@ -14,11 +14,14 @@
 //
 // Kernels.  prepare: FP64 row norms (stored as FP32) and the BF16 planes,
 // K padded to a multiple of 64.  gram: persistent, one CTA per SM, 128 x 128
-// pair tiles taken in lambda order (Eq. eq_gmap) as one contiguous run of
-// tile numbers per CTA, so consecutive tiles share their row block and the
-// CTA keeps that row block's planes (A) resident in shared memory while TMA
-// streams the column blocks (B) through a ring of stages, one per 64-wide K
-// chunk (all planes).  Warp 0 issues TMA,
+// pair tiles taken in lambda order (Eq. eq_gmap): first one contiguous run of
+// tile numbers per CTA, then short runs taken from a global counter by
+// whichever CTA is free (SMs do not all store at the same rate), so
+// consecutive tiles mostly share their row block and the CTA keeps that row
+// block's planes (A) resident in shared memory while TMA streams the column
+// blocks (B) through a ring of 16 KB stages, one plane of one 64-wide K chunk each.
+// Warp 0 takes the tiles and passes them to the other roles through a small
+// queue in shared memory, and issues TMA,
 // warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator (with the
 // column block as the M operand, so TMEM lanes are output columns), warps
 // 2-17 read TMEM back, form the distances, flag cancellations and store each
@@ -49,7 +52,12 @@ constexpr int STG_ROWS = 8;                // rows staged at a time by a row gro
 constexpr int STG_LD = TILE + 4;           // staging row: 128 distances shifted by the row's 16-byte phase
 constexpr int STG_FLOATS = STG_ROWS * STG_LD;  // per row group
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
+constexpr int TQ = 8;                      // tile queue slots (producer -> MMA and epilogue)
+constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last tile
+constexpr uint32_t STATIC_PCT = 80;        // share of the tiles assigned up front, in contiguous runs
+constexpr uint32_t DYN_CHUNK = 8;          // tiles per grab from the global counter afterwards
 constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int MAX_STAGES = 12;             // B ring depth cap (16 KB stages)
 
 constexpr float TAU_X6 = 0.3125f;  // flag threshold for hi/mid/lo (derived bound)
 constexpr float TAU_X3 = 0.0625f;  // flag threshold for hi/lo (empirical)
@@ -59,7 +67,8 @@ struct WsLayout {
     unsigned long long cap;
 };
 
-// Workspace: [header 256 B: flag counter, status][norms n FP32][planes
+// Workspace: [header 256 B: flag counter (u64 at 0), status (int at 8), tile
+// counter (u64 at 16)][norms n FP32][planes
 // P x n x dp BF16][flag list cap x u64], each part 256-byte aligned.
 WsLayout ws_layout(uint32_t n, uint32_t d, int prec)
 {
@@ -235,11 +244,15 @@ struct GramArgs {
     uint32_t n, nkc;           // points, 64-wide K chunks
     uint32_t m;                // tile rows of the triangle
     uint64_t ntiles;           // tile numbers walked: m(m+1)/2 (lambda) or m*m (BB)
+    uint64_t static_per;       // tile numbers per CTA in its up-front run
+    uint64_t dyn_start;        // first tile number handed out by the counter
+    uint32_t chunk;            // tile numbers per grab from the counter
     uint32_t stages;           // B ring depth
     float tau;
     const float *norms;
     float *out;
     unsigned long long *flag_count, *flag_list, flag_cap;
+    unsigned long long *tile_counter;  // zero at launch
     int *status;
 };
 
@@ -298,12 +311,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;
-    const uint32_t stage_bytes = (uint32_t)P * CHUNK_BYTES;
+    constexpr uint32_t stage_bytes = CHUNK_BYTES;            // one plane of one K chunk
+    constexpr uint32_t stg_floats = P == 2 ? (NEPI / 4) * STG_FLOATS : 0;  // staging rows (P = 2 only)
     const uint32_t sA = base;                                  // [kc][p] chunks
-    const uint32_t sB = base + a_bytes;                        // [stage][p] chunks: one K chunk, all planes
+    const uint32_t sB = base + a_bytes;                        // [stage] chunks of one plane
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
     float *stage_base = epi + NEPI * NORM_FLOATS;  // one staging area per row group
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage_base + (NEPI / 4) * STG_FLOATS);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage_base + stg_floats);
     // barriers: fullA, freeA, done, tmem_full[2], tmem_empty[2], fullB[stages], emptyB[stages]
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t b_fullA = bar0, b_freeA = bar0 + 8, b_done = bar0 + 16;
@@ -311,6 +325,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t b_fullB = bar0 + 56, b_emptyB = bar0 + 56 + 8 * g.stages;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
+    // tile queue: entry (bi << 32 | bj), or TQ_END; full: one arrival by the
+    // producer, empty: one by the MMA thread and one per epilogue warp
+    __shared__ volatile unsigned long long s_tq[TQ];
+    __shared__ __align__(8) uint64_t s_tqbar[2 * TQ];
+    const uint32_t b_tqfull = smem_u32(s_tqbar), b_tqempty = b_tqfull + 8 * TQ;
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -326,6 +345,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(b_fullB + 8 * s, 1);
             mbar_init(b_emptyB + 8 * s, 1);
         }
+        for (int s = 0; s < TQ; ++s) {
+            mbar_init(b_tqfull + 8 * s, 1);
+            mbar_init(b_tqempty + 8 * s, 1 + NEPI);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -338,10 +361,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    // this CTA's contiguous run of tile numbers
-    const uint64_t per = (g.ntiles + gridDim.x - 1) / gridDim.x;
-    const uint64_t t0 = (uint64_t)blockIdx.x * per;
-    const uint64_t t1 = t0 + per < g.ntiles ? t0 + per : g.ntiles;
+    // Queue entry k sits in slot k % TQ; its fill is phase k / TQ of the slot's barriers.
+    auto tq_push = [&](uint32_t k, unsigned long long v) {
+        const uint32_t slot = k % TQ;
+        if (!mbar_wait(b_tqempty + 8 * slot, ((k / TQ) & 1) ^ 1, &s_abort)) return false;
+        s_tq[slot] = v;
+        mbar_arrive(b_tqfull + 8 * slot);
+        return true;
+    };
+    // by one thread (the MMA issuer)
+    auto tq_pop = [&](uint32_t k, unsigned long long &v) {
+        const uint32_t slot = k % TQ;
+        if (!mbar_wait(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort)) return false;
+        v = s_tq[slot];
+        mbar_arrive(b_tqempty + 8 * slot);
+        return true;
+    };
+    // by a whole epilogue warp: lane 0 waits, reads and releases the slot, then
+    // broadcasts the entry
+    auto tq_pop_warp = [&](uint32_t k, unsigned long long &v) {
+        unsigned long long r = 0;
+        int ok = 0;
+        if ((threadIdx.x & 31) == 0) {
+            const uint32_t slot = k % TQ;
+            ok = mbar_wait(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort) ? 1 : 0;
+            if (ok) {
+                r = s_tq[slot];
+                mbar_arrive(b_tqempty + 8 * slot);
+            }
+        }
+        v = __shfl_sync(0xffffffffu, r, 0);
+        return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
 
     // The TMA and MMA roles run on lane 0 of their warps.  Between two MMAs
     // the issuing thread does nothing but add descriptor offsets: a
@@ -353,11 +404,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
-            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, loads = 0;
+            uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, loads = 0, k = 0;
             bool ok = true;
-            for (uint64_t t = t0; t < t1 && ok; ++t) {
+            // this CTA's up-front run of tile numbers, then runs from the counter
+            uint64_t t = (uint64_t)blockIdx.x * g.static_per, tend = t + g.static_per;
+            while (ok) {
+                if (t >= tend) {
+                    t = g.dyn_start + atomicAdd(g.tile_counter, (unsigned long long)g.chunk);
+                    if (t >= g.ntiles) break;
+                    tend = t + g.chunk < g.ntiles ? t + g.chunk : g.ntiles;
+                }
                 uint32_t bi, bj;
-                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+                if (!tile_of<MAP>(t++, g.m, bi, bj)) continue;
+                if (!tq_push(k++, ((unsigned long long)bi << 32) | bj)) {
+                    ok = false;
+                    break;
+                }
                 if (bi != a_row) {
                     if (a_loads > 0 && !mbar_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
                         ok = false;
@@ -370,22 +432,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     ++a_loads;
                     a_row = bi;
                 }
-                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
-                    if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(b_fullB + 8 * stage, stage_bytes);
-                    for (int p = 0; p < P; ++p)
-                        tma_load_3d(sB + (stage * P + p) * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH,
-                                    bj * TILE, p);
-                    ++loads;
-                    if (++stage == g.stages) {
-                        stage = 0;
-                        b_phase ^= 1;
+                for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
+                    for (int p = 0; p < P; ++p) {
+                        if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(b_fullB + 8 * stage, stage_bytes);
+                        tma_load_3d(sB + stage * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH, bj * TILE, p);
+                        ++loads;
+                        if (++stage == g.stages) {
+                            stage = 0;
+                            b_phase ^= 1;
+                        }
                     }
                 }
             }
+            if (ok) ok = tq_push(k, TQ_END);
             if (!ok) {
                 s_abort = 1;
                 atomicExch(g.status, (int)TRI_ETIMEOUT);
@@ -406,9 +469,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint64_t a_desc0 = ((uint64_t)kDescHi << 32) | sdesc_lo(sA);
             const uint64_t b_desc0 = ((uint64_t)kDescHi << 32) | sdesc_lo(sB);
             constexpr uint32_t CH16 = CHUNK_BYTES >> 4;  // one 16 KB chunk in descriptor units
-            for (uint64_t t = t0; t < t1 && ok; ++t) {
-                uint32_t bi, bj;
-                if (!tile_of<MAP>(t, g.m, bi, bj)) continue;
+            for (uint32_t k = 0;; ++k) {
+                unsigned long long v;
+                if (!tq_pop(k, v)) {
+                    ok = false;
+                    break;
+                }
+                if (v == TQ_END) break;
+                const uint32_t bi = (uint32_t)(v >> 32);
                 if (bi != a_row) {
                     if (a_loads > 0) umma_commit(b_freeA);  // old A is free once issued MMAs finish
                     if (!mbar_wait(b_fullA, a_loads & 1, &s_abort)) {
@@ -424,28 +492,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + acc * TILE;
-                for (uint32_t kc = 0; kc < g.nkc; ++kc) {
-                    if (!mbar_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
+                for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
                     const uint64_t a_desc = a_desc0 + kc * P * CH16;
-                    const uint64_t b_desc = b_desc0 + stage * P * CH16;
 #pragma unroll
-                    for (int pb = 0; pb < P; ++pb)
+                    for (int pb = 0; pb < P; ++pb) {
+                        if (!mbar_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t b_desc = b_desc0 + stage * CH16;
 #pragma unroll
                         for (int pa = 0; pa + pb < P; ++pa)
 #pragma unroll
                             for (int kk = 0; kk < KCH / 16; ++kk)
                                 // the column tile is the M operand: TMEM lane = output column;
                                 // +2 per 16-element K step (32 bytes in 16-byte units)
-                                umma_bf16(d_tmem, b_desc + pb * CH16 + 2 * kk, a_desc + pa * CH16 + 2 * kk,
+                                umma_bf16(d_tmem, b_desc + 2 * kk, a_desc + pa * CH16 + 2 * kk,
                                           (kc | pb | pa | kk) ? 1u : 0u);
-                    umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
-                    if (++stage == g.stages) {
-                        stage = 0;
-                        b_phase ^= 1;
+                        umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
+                        if (++stage == g.stages) {
+                            stage = 0;
+                            b_phase ^= 1;
+                        }
                     }
                 }
                 if (!ok) break;
@@ -480,17 +549,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float *snorm = epi + e * NORM_FLOATS;     // norms of this warp's rows, two buffers
         float *stg = stage_base + grp * STG_FLOATS;  // this row group's staging rows
         const float tau = g.tau;
-        auto next_valid = [&](uint64_t t) {
-            uint32_t a, b;
-            while (t < t1 && !tile_of<MAP>(t, g.m, a, b)) ++t;
-            return t;
-        };
         // next tile's norms: lane l holds the norms of row l % 16 of chunks
         // u = 2v + l / 16 (16 rows each) and of its own column
         float pfr[NCH / 2], pfj = 0.0f;
-        auto prefetch = [&](uint64_t t) {
-            uint32_t a, b;
-            tile_of<MAP>(t, g.m, a, b);
+        auto prefetch = [&](unsigned long long tv) {
+            const uint32_t a = (uint32_t)(tv >> 32), b = (uint32_t)tv;
 #pragma unroll
             for (int v = 0; v < NCH / 2; ++v) {
                 const uint32_t u = 2 * v + (lane >> 4);
@@ -500,19 +563,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t jj = b * TILE + q * 32 + lane;
             pfj = jj < g.n ? __ldg(g.norms + jj) : 0.0f;
         };
-        uint32_t acc = 0, acc_phase = 0, nbuf = 0;
-        uint64_t t = next_valid(t0);
-        if (t < t1) prefetch(t);
-        while (t < t1) {
-            uint32_t bi, bj;
-            tile_of<MAP>(t, g.m, bi, bj);
+        uint32_t acc = 0, acc_phase = 0, nbuf = 0, k = 0;
+        auto fail = [&]() {
+            if (lane == 0) {
+                s_abort = 1;
+                atomicExch(g.status, (int)TRI_ETIMEOUT);
+            }
+        };
+        unsigned long long cur;
+        if (!tq_pop_warp(k++, cur)) {
+            fail();
+            cur = TQ_END;
+        }
+        if (cur != TQ_END) prefetch(cur);
+        while (cur != TQ_END) {
+            const uint32_t bi = (uint32_t)(cur >> 32), bj = (uint32_t)cur;
             float *rn = snorm + nbuf * 32;  // this tile's row norms: [chunk u][16]
 #pragma unroll
             for (int v = 0; v < NCH / 2; ++v) rn[32 * v + lane] = pfr[v];
             const float nj = pfj;
             __syncwarp();
-            const uint64_t tn = next_valid(t + 1);
-            if (tn < t1) prefetch(tn);
+            unsigned long long nxt;
+            if (!tq_pop_warp(k++, nxt)) {
+                fail();
+                break;
+            }
+            if (nxt != TQ_END) prefetch(nxt);
             if (!warp_wait(b_tfull + 8 * acc, acc_phase, &s_abort)) {
                 if (lane == 0) {
                     s_abort = 1;
@@ -634,7 +710,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 acc_phase ^= 1;
             }
             nbuf ^= 1;
-            t = tn;
+            cur = nxt;
         }
     }
     tc_fence_before();
@@ -724,10 +800,11 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.P = prec == TRI_BF16X6 ? 3 : 2;
     p.dp = (d + KCH - 1) / KCH * KCH;
     p.nkc = p.dp / KCH;
-    const size_t fixed = 1024 /*align*/ + (NEPI * NORM_FLOATS + (NEPI / 4) * STG_FLOATS) * 4 + 8 * (7 + 2 * 8);
-    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = (size_t)p.P * CHUNK_BYTES;
+    const size_t stg = p.P == 2 ? (size_t)(NEPI / 4) * STG_FLOATS : 0;
+    const size_t fixed = 1024 /*align*/ + (NEPI * NORM_FLOATS + stg) * 4 + 8 * (7 + 2 * MAX_STAGES);
+    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
-    p.stages = (uint32_t)std::min<size_t>(8, (SMEM_LIMIT - fixed - a) / st);
+    p.stages = (uint32_t)std::min<size_t>(MAX_STAGES, (SMEM_LIMIT - fixed - a) / st);
     p.smem = fixed + a + p.stages * st;
     return true;
 }
@@ -799,10 +876,15 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     g.out = out;
     g.flag_count = (unsigned long long *)(ws + L.hdr);
     g.status = (int *)(ws + L.hdr + 8);
+    g.tile_counter = (unsigned long long *)(ws + L.hdr + 16);
     g.flag_list = (unsigned long long *)(ws + L.flags);
     g.flag_cap = L.cap;
     const uint32_t grid = (uint32_t)std::min<uint64_t>(num_sms(), ntiles);
+    g.static_per = ntiles * STATIC_PCT / 100 / grid;
+    g.dyn_start = g.static_per * grid;
+    g.chunk = DYN_CHUNK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(g.tile_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return TRI_ECUDA;
     cudaError_t e;
 #define TRI_G(MP, PP)                                                                                          \
     e = cudaFuncSetAttribute(gram_kernel<MP, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);  \
