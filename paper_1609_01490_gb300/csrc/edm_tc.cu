@@ -24,8 +24,9 @@
 // queue in shared memory, and issues TMA,
 // warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator (with the
 // column block as the M operand, so TMEM lanes are output columns), warps
-// 2-17 read TMEM back, form the distances, flag cancellations and store each
-// packed row segment with one coalesced store per warp.  fixup: FP64
+// 2-17 read TMEM back, form the distances, flag cancellations and store the
+// packed row segments (P = 2: whole segments through shared memory; P = 3:
+// one coalesced 128-byte store per warp and row).  fixup: FP64
 // recompute of the flagged pairs.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -50,7 +51,7 @@ constexpr int EPI_ROWS = 16;               // output rows per TMEM load in the e
 constexpr int NORM_FLOATS = 2 * 32;       // per epilogue warp: norms of its 32 rows of the tile (double buffered)
 constexpr int STG_ROWS = 8;                // rows staged at a time by a row group
 constexpr int STG_LD = TILE + 4;           // staging row: 128 distances shifted by the row's 16-byte phase
-constexpr int STG_FLOATS = STG_ROWS * STG_LD;  // per row group
+constexpr int STG_FLOATS = STG_ROWS * STG_LD;  // one staging buffer
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 constexpr int TQ = 8;                      // tile queue slots (producer -> MMA and epilogue)
 constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last tile
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;
     constexpr uint32_t stage_bytes = CHUNK_BYTES;            // one plane of one K chunk
-    constexpr uint32_t stg_floats = P == 2 ? (NEPI / 4) * STG_FLOATS : 0;  // staging rows (P = 2 only)
+    constexpr uint32_t stg_floats = P == 2 ? (NEPI / 4) * 2 * STG_FLOATS : 0;  // two staging buffers per row group
     const uint32_t sA = base;                                  // [kc][p] chunks
     const uint32_t sB = base + a_bytes;                        // [stage] chunks of one plane
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
@@ -397,9 +398,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // The TMA and MMA roles run on lane 0 of their warps.  Between two MMAs
     // the issuing thread does nothing but add descriptor offsets: a
     // 128x128x16 MMA takes about 68 cycles, and any longer gap in the issue
-    // stream leaves the tensor pipe idle.  Each stage holds one 64-wide K
-    // chunk of all planes of the column block, so the MMA thread waits once
-    // per 4 P(P+1)/2 MMAs.
+    // stream leaves the tensor pipe idle.  Each stage holds one plane of one
+    // 64-wide K chunk of the column block: the MMA thread waits once per
+    // 4 (P - pb) MMAs for column plane pb.
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
@@ -547,7 +548,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         constexpr int NCH = TILE / EPI_ROWS / NG;   // 16-row chunks per warp and tile
         const uint32_t e = warp - 2, q = warp & 3, grp = e >> 2;
         float *snorm = epi + e * NORM_FLOATS;     // norms of this warp's rows, two buffers
-        float *stg = stage_base + grp * STG_FLOATS;  // this row group's staging rows
+        float *stg = stage_base + grp * 2 * STG_FLOATS;  // this row group's two staging buffers
+        uint32_t hc = 0;                                   // halves staged so far (selects the buffer)
         const float tau = g.tau;
         // next tile's norms: lane l holds the norms of row l % 16 of chunks
         // u = 2v + l / 16 (16 rows each) and of its own column
@@ -645,47 +647,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 if constexpr (P == 2) {
-                    // Store through shared memory in two halves of 8 rows: the row
-                    // group's four warps (one per 32-column quarter) write their
-                    // columns of each row into a staging row shifted by the row's
-                    // 16-byte phase (T2(i0 + k) mod 4, which depends on k only since
-                    // i0 is a multiple of 16); then each warp writes two whole row
-                    // segments, the aligned middle with one float4 per lane and the
-                    // ends with scalar stores.  Every 128-byte line of a segment's
-                    // middle is then written by one instruction.
-    #pragma unroll
-                    for (int half = 0; half < EPI_ROWS / STG_ROWS; ++half) {
-    #pragma unroll
-                        for (int kk = 0; kk < STG_ROWS; ++kk) {
-                            const int k = half * STG_ROWS + kk;
-                            stg[kk * STG_LD + row_phase(k) + q * 32 + lane] = dv[k];
-                        }
-                        named_sync(1 + grp, 128);
-    #pragma unroll
-                        for (int r2 = 0; r2 < STG_ROWS / 4; ++r2) {
-                            const uint32_t kk = q * (STG_ROWS / 4) + r2, k = half * STG_ROWS + kk, i = i0 + k;
-                            if (i < g.n) {
-                                const uint32_t len = bi == bj ? i - bj * TILE + 1 : TILE;  // columns of row i here
-                                float *seg = g.out + T2(i) + bj * TILE;
-                                const uint32_t ph = row_phase(k), head = (4 - ph) & 3;
-                                const float *src = stg + kk * STG_LD + ph;
-                                const uint32_t h = head < len ? head : len;
-                                const uint32_t nv = (len - h) >> 2;
-                                if (lane < nv)
-                                    __stcs(reinterpret_cast<float4 *>(seg + h) + lane,
-                                           *reinterpret_cast<const float4 *>(src + h + 4 * lane));
-                                const uint32_t t0 = h + 4 * nv, tail = len - t0;  // h <= 3, tail <= 3
-                                if (lane < h) __stcs(seg + lane, src[lane]);
-                                if (lane >= 4 && lane - 4 < tail) __stcs(seg + t0 + lane - 4, src[t0 + lane - 4]);
-                            }
-                        }
-                        named_sync(1 + grp, 128);
+                // Store through shared memory in two halves of 8 rows: the row
+                // group's four warps (one per 32-column quarter) write their
+                // columns of each row into a staging row shifted by the row's
+                // 16-byte phase (T2(i0 + k) mod 4, which depends on k only since
+                // i0 is a multiple of 16); then each warp writes two whole row
+                // segments, the aligned middle with one float4 per lane and the
+                // ends with scalar stores, so every 128-byte line of a segment's
+                // middle is written by one instruction.  The two staging buffers
+                // alternate: the barrier before a half's stores also tells each
+                // warp that the group has finished reading the buffer it will
+                // fill next, so one barrier per half suffices.
+#pragma unroll
+                for (int half = 0; half < EPI_ROWS / STG_ROWS; ++half) {
+                    float *sb = stg + (hc & 1) * STG_FLOATS;
+                    ++hc;
+#pragma unroll
+                    for (int kk = 0; kk < STG_ROWS; ++kk) {
+                        const int k = half * STG_ROWS + kk;
+                        sb[kk * STG_LD + row_phase(k) + q * 32 + lane] = dv[k];
                     }
+                    named_sync(1 + grp, 128);
+#pragma unroll
+                    for (int r2 = 0; r2 < STG_ROWS / 4; ++r2) {
+                        const uint32_t kk = q * (STG_ROWS / 4) + r2, k = half * STG_ROWS + kk, i = i0 + k;
+                        if (i < g.n) {
+                            const uint32_t len = bi == bj ? i - bj * TILE + 1 : TILE;  // columns of row i here
+                            float *seg = g.out + T2(i) + bj * TILE;
+                            const uint32_t ph = row_phase(k), head = (4 - ph) & 3;
+                            const float *src = sb + kk * STG_LD + ph;
+                            const uint32_t h = head < len ? head : len;
+                            const uint32_t nv = (len - h) >> 2;
+                            if (lane < nv)
+                                __stcs(reinterpret_cast<float4 *>(seg + h) + lane,
+                                       *reinterpret_cast<const float4 *>(src + h + 4 * lane));
+                            const uint32_t t0 = h + 4 * nv, tail = len - t0;  // h <= 3, tail <= 3
+                            if (lane < h) __stcs(seg + lane, src[lane]);
+                            if (lane >= 4 && lane - 4 < tail) __stcs(seg + t0 + lane - 4, src[t0 + lane - 4]);
+                        }
+                    }
+                }
                 } else {
                     // Direct stores: for each row the warp's 32 lanes hold 32
                     // consecutive packed entries, written by one 128-byte store.
-                    // (Measured faster than staging for P = 3, whose MMA stream
-                    // rather than its stores bounds the kernel.)
+                    // For P = 3 the tensor core's operand reads already take most
+                    // of the shared-memory bandwidth, and staging (which also
+                    // costs two operand stages) measured slower.
                     float *row = g.out + T2(i0) + j;  // row i0, column j
                     if (bi != bj && (bi + 1) * TILE <= g.n) {
 #pragma unroll
@@ -800,7 +807,7 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.P = prec == TRI_BF16X6 ? 3 : 2;
     p.dp = (d + KCH - 1) / KCH * KCH;
     p.nkc = p.dp / KCH;
-    const size_t stg = p.P == 2 ? (size_t)(NEPI / 4) * STG_FLOATS : 0;
+    const size_t stg = p.P == 2 ? (size_t)(NEPI / 4) * 2 * STG_FLOATS : 0;  // P = 2 stages its stores
     const size_t fixed = 1024 /*align*/ + (NEPI * NORM_FLOATS + stg) * 4 + 8 * (7 + 2 * MAX_STAGES);
     const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
