@@ -13,21 +13,24 @@
 // flagged pairs in FP64 by direct differences (the paper's definition).
 //
 // Kernels.  prepare: FP64 row norms (stored as FP32) and the BF16 planes,
-// K padded to a multiple of 64.  gram: persistent, one CTA per SM, 128 x 128
-// pair tiles taken in lambda order (Eq. eq_gmap): first one contiguous run of
-// tile numbers per CTA, then short runs taken from a global counter by
-// whichever CTA is free (SMs do not all store at the same rate), so
-// consecutive tiles mostly share their row block and the CTA keeps that row
-// block's planes (A) resident in shared memory while TMA streams the column
-// blocks (B) through a ring of 16 KB stages, one plane of one 64-wide K chunk each.
-// Warp 0 takes the tiles and passes them to the other roles through a small
-// queue in shared memory, and issues TMA,
-// warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator (with the
-// column block as the M operand, so TMEM lanes are output columns), warps
-// 2-17 read TMEM back, form the distances, flag cancellations and store the
-// packed row segments (P = 2: whole segments through shared memory; P = 3:
-// one coalesced 128-byte store per warp and row).  fixup: FP64
-// recompute of the flagged pairs.
+// K padded to a multiple of 64.  gram: persistent clusters of two CTAs on two
+// SMs (a CTA pair), one pair per two SMs.  A unit of work is a 2 x 2 block of
+// 128 x 128 pair tiles (row blocks 2R, 2R + 1, column blocks 2C, 2C + 1),
+// taken in lambda order over the triangle of units (Eq. eq_gmap): first one
+// contiguous run of units per pair, then short runs from a global counter by
+// whichever pair is free.  CTA r keeps row block 2R + r resident in shared
+// memory (the planes of A, reloaded when R changes) and streams column block
+// 2C + r through a ring of 16 KB TMA stages, one plane of one 64-wide K chunk
+// each.  One thread of the even CTA issues tcgen05.mma.cta_group::2 with M =
+// 256 (the two column blocks), N = 256 (the two row blocks), K = 16, so each
+// instruction does 128 x 256 x 16 on each SM; each CTA's TMEM receives its
+// column block x both row blocks, double buffered (2 x 256 columns).  Warp 0
+// of the even CTA takes the units and passes them to both CTAs' roles through
+// a small queue in shared memory (written across the pair); warp 0 of each CTA
+// issues its TMA; warps 2-17 of each CTA read TMEM back (lanes = output
+// columns), form the distances, flag cancellations and store the packed row
+// segments (P = 2: whole segments through shared memory; P = 3: one coalesced
+// 128-byte store per warp and row).  fixup: FP64 recompute of the flagged pairs.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -97,11 +100,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -120,6 +118,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+// As mbar_try, with acquire at cluster scope: for barriers that the other CTA
+// of the pair arrives on with release at cluster scope.
+__device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
@@ -131,12 +144,14 @@ __device__ __forceinline__ uint64_t global_ns()
 // WAIT_LIMIT_NS, or early when another role has already given up (unless
 // abort_flag is null: the drain waits at exit must not cut short a copy or
 // MMA that is still writing).
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
 {
-    if (mbar_try(bar, parity)) return true;
+    auto test = [&]() { return CL ? mbar_try_cl(bar, parity) : mbar_try(bar, parity); };
+    if (test()) return true;
     const uint64_t start = global_ns();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try(bar, parity)) return true;
+        if (test()) return true;
         if ((it & 15) == 0) {
             if (abort_flag && *abort_flag) return false;
             if (global_ns() - start > WAIT_LIMIT_NS) return false;
@@ -147,42 +162,123 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 
 // mbar_wait by lane 0 with the result broadcast, so the whole warp leaves
 // together and agrees on it.
+template <bool CL = false>
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
 {
     int r = 0;
-    if ((threadIdx.x & 31) == 0) r = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) r = mbar_wait<CL>(bar, parity, abort_flag) ? 1 : 0;
     return __shfl_sync(0xffffffffu, r, 0) != 0;
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
-                                            int z)
+// ------------------------------------------------------- CTA pair ----
+// The Gram kernel runs as clusters of two CTAs on two SMs (a CTA pair).
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// All threads of both CTAs; orders earlier shared-memory writes (and barrier
+// initialisation) before later accesses by the other CTA.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Arrive on a barrier given by its cluster address (own or the other CTA's),
+// with release at CTA scope: it orders nothing of this thread's other memory
+// traffic for the other CTA, and so does not wait for this thread's pending
+// global stores (a cluster-scope release would).  Used where the waiting side
+// needs no data from this thread (tcgen05 fences order the TMEM reads).
+__device__ __forceinline__ void mbar_arrive_cl(uint32_t cl_bar)
+{
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cl_bar) : "memory");
+}
+
+// Arrive with release at cluster scope: orders this thread's earlier stores
+// into the other CTA's shared memory before the arrival.
+__device__ __forceinline__ void mbar_arrive_cl_release(uint32_t cl_bar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void st_cl_u64(uint32_t cl_addr, unsigned long long v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cl_addr), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cl_s32(uint32_t cl_addr, int v)
+{
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(cl_addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_cl_u32(uint32_t cl_addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cl_addr) : "memory");
+    return v;
+}
+
+// TMA tile load into this CTA's shared memory whose completion (bytes) is
+// counted on a barrier of either CTA of the pair (cl_bar: cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, uint32_t cl_bar, int x, int y,
+                                                 int z)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(cl_bar)
         : "memory");
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 128 (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16).
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
-                           ((uint32_t)(TILE >> 4) << 24);
+// Instruction descriptor, kind::f16 across the CTA pair: FP32 accumulator,
+// BF16 A and B, both K-major, N = 256 (bits 17-22 hold N/8), M = 256 (bits
+// 24-28 hold M/16).  Rows 0-127 of M (and of N) come from the even CTA,
+// 128-255 from the odd one; each CTA's TMEM receives its own 128 rows of M
+// across all 256 columns of N.
+constexpr uint32_t IDESC2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * TILE) >> 3) << 17) |
+                            ((uint32_t)((2 * TILE) >> 4) << 24);
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
+// One MMA over the pair: A (M side) and B (N side) are read at the same
+// shared-memory offsets in both CTAs; each CTA holds half of A's M rows and
+// half of B's N rows.
+__device__ __forceinline__ void umma2_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC2), "r"(accumulate)
         : "memory");
 }
 
-__device__ __forceinline__ void umma_commit(uint32_t bar)
+// Arrive on the barrier at this offset in both CTAs once the issued MMAs finish.
+__device__ __forceinline__ void umma2_commit_both(uint32_t bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+// Arrive on the issuing CTA's barrier once the issued MMAs finish.
+__device__ __forceinline__ void umma2_commit_own(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -241,13 +337,18 @@ __global__ void prepare_kernel(const float *__restrict__ x, uint32_t n, uint32_t
 }
 
 // --------------------------------------------------------------- gram ----
+// A unit is a 2 x 2 block of tiles: row blocks 2R, 2R + 1 and column blocks
+// 2C, 2C + 1.  CTA r of the pair holds row block 2R + r (half of the MMA's N
+// side) and streams column block 2C + r (half of its M side); its accumulator
+// covers the tiles (2R, 2C + r) and (2R + 1, 2C + r).
 struct GramArgs {
     uint32_t n, nkc;           // points, 64-wide K chunks
     uint32_t m;                // tile rows of the triangle
-    uint64_t ntiles;           // tile numbers walked: m(m+1)/2 (lambda) or m*m (BB)
-    uint64_t static_per;       // tile numbers per CTA in its up-front run
-    uint64_t dyn_start;        // first tile number handed out by the counter
-    uint32_t chunk;            // tile numbers per grab from the counter
+    uint32_t mb;               // unit rows: ceil(m / 2)
+    uint64_t nunits;           // units walked: lambda over the mb-row triangle or the mb x mb box
+    uint64_t static_per;       // units per CTA pair in its up-front run
+    uint64_t dyn_start;        // first unit handed out by the counter
+    uint32_t chunk;            // units per grab from the counter
     uint32_t stages;           // B ring depth
     float tau;
     const float *norms;
@@ -257,16 +358,18 @@ struct GramArgs {
     int *status;
 };
 
+// Unit number u -> (R, C): lambda over the triangle of units (Eq. eq_gmap),
+// or row-major over the mb x mb box with units above the diagonal skipped.
 template <int MAP>
-__device__ __forceinline__ bool tile_of(uint64_t t, uint32_t m, uint32_t &bi, uint32_t &bj)
+__device__ __forceinline__ bool unit_of(uint64_t u, uint32_t mb, uint32_t &R, uint32_t &C)
 {
     if constexpr (MAP == MAP_LAMBDA) {
-        lambda_diag<TRI_SQRT_R>((uint32_t)t, bi, bj);
+        lambda_diag<TRI_SQRT_R>((uint32_t)u, R, C);
         return true;
     } else {
-        bi = (uint32_t)(t / m);
-        bj = (uint32_t)(t - (uint64_t)bi * m);
-        return bj <= bi;  // bounding box: tiles above the diagonal are skipped
+        R = (uint32_t)(u / mb);
+        C = (uint32_t)(u - (uint64_t)R * mb);
+        return C <= R;
     }
 }
 
@@ -303,21 +406,21 @@ constexpr uint32_t kDescHi = (1024u >> 4) | (1u << 14) | (2u << 29);  // SBO, ve
 
 
 template <int MAP, int P>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     gram_kernel(const __grid_constant__ CUtensorMap tmap, const GramArgs g)
 {
     extern __shared__ uint8_t smem_raw[];
-    // 1024-byte aligned operand area
+    // 1024-byte aligned operand area, at the same offsets in both CTAs
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;
-    constexpr uint32_t stage_bytes = CHUNK_BYTES;            // one plane of one K chunk
+    const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;  // this CTA's row block
+    constexpr uint32_t stage_bytes = CHUNK_BYTES;               // one plane of one K chunk
     constexpr uint32_t stg_floats = P == 2 ? (NEPI / 4) * 2 * STG_FLOATS : 0;  // two staging buffers per row group
-    const uint32_t sA = base;                                  // [kc][p] chunks
-    const uint32_t sB = base + a_bytes;                        // [stage] chunks of one plane
+    const uint32_t sA = base;                                   // [kc][p] chunks
+    const uint32_t sB = base + a_bytes;                         // [stage] chunks of one plane
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
-    float *stage_base = epi + NEPI * NORM_FLOATS;  // one staging area per row group
+    float *stage_base = epi + NEPI * NORM_FLOATS;  // staging area of the row groups
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage_base + stg_floats);
     // barriers: fullA, freeA, done, tmem_full[2], tmem_empty[2], fullB[stages], emptyB[stages]
     const uint32_t bar0 = smem_u32(bars);
@@ -326,13 +429,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t b_fullB = bar0 + 56, b_emptyB = bar0 + 56 + 8 * g.stages;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
-    // tile queue: entry (bi << 32 | bj), or TQ_END; full: one arrival by the
-    // producer, empty: one by the MMA thread and one per epilogue warp
+    // unit queue: entry (R << 32 | C), or TQ_END, written by the even CTA's
+    // producer into both CTAs
     __shared__ volatile unsigned long long s_tq[TQ];
     __shared__ __align__(8) uint64_t s_tqbar[2 * TQ];
     const uint32_t b_tqfull = smem_u32(s_tqbar), b_tqempty = b_tqfull + 8 * TQ;
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank(), other = rank ^ 1u;
+    const bool leader = rank == 0;  // the even CTA issues the pair's MMAs
+    // Barriers that count work of both CTAs live in the even CTA: fullA and
+    // fullB (one expect_tx arrival by the even CTA for both CTAs' bytes: the
+    // odd CTA's copies may land before it, which only takes the transaction
+    // count below zero until the arrival), tmem_empty
+    // (every epilogue warp of both) and the queue's empty barriers (the even
+    // CTA's MMA thread and epilogue warps, the odd CTA's producer and epilogue
+    // warps).  freeA, emptyB and tmem_full receive one multicast commit in each CTA.
     if (threadIdx.x == 0) {
         s_abort = 0;
         mbar_init(b_fullA, 1);
@@ -340,7 +452,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(b_done, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
-            mbar_init(b_tempty + 8 * i, NEPI);  // one arrival per epilogue warp
+            mbar_init(b_tempty + 8 * i, 2 * NEPI);
         }
         for (uint32_t s = 0; s < g.stages; ++s) {
             mbar_init(b_fullB + 8 * s, 1);
@@ -348,34 +460,56 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int s = 0; s < TQ; ++s) {
             mbar_init(b_tqfull + 8 * s, 1);
-            mbar_init(b_tqempty + 8 * s, 1 + NEPI);
+            mbar_init(b_tqempty + 8 * s, 2 + 2 * NEPI);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&s_tmem))
+        // one warp in each CTA of the pair allocates (the pair's accumulators
+        // sit at the same TMEM address in both)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_tmem))
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    // The MMAs address both CTAs' accumulators with the even CTA's address:
+    // run only if the two allocations agree.
+    const bool run = ld_cl_u32(mapa(smem_u32(&s_tmem), other)) == tmem;
+    if (!run && threadIdx.x == 0) atomicExch(g.status, (int)TRI_ECUDA);
+
+    // cluster addresses of the even CTA's shared barriers and of the other CTA's queue
+    const uint32_t L_fullA = mapa(b_fullA, 0), L_fullB = mapa(b_fullB, 0), L_tempty = mapa(b_tempty, 0);
+    const uint32_t L_tqempty = mapa(b_tqempty, 0);
+    const uint32_t O_tqfull = mapa(b_tqfull, other), O_tq = mapa(smem_u32((const void *)s_tq), other);
+    const uint32_t O_abort = mapa(smem_u32((const void *)&s_abort), other);
+    // a failed wait stops both CTAs of the pair
+    auto give_up = [&]() {
+        s_abort = 1;
+        st_cl_s32(O_abort, 1);
+        atomicExch(g.status, (int)TRI_ETIMEOUT);
+    };
 
     // Queue entry k sits in slot k % TQ; its fill is phase k / TQ of the slot's barriers.
+    // Pushed by the even CTA's producer into both CTAs.
     auto tq_push = [&](uint32_t k, unsigned long long v) {
         const uint32_t slot = k % TQ;
         if (!mbar_wait(b_tqempty + 8 * slot, ((k / TQ) & 1) ^ 1, &s_abort)) return false;
         s_tq[slot] = v;
         mbar_arrive(b_tqfull + 8 * slot);
+        st_cl_u64(O_tq + 8 * slot, v);
+        mbar_arrive_cl_release(O_tqfull + 8 * slot);
         return true;
     };
-    // by one thread (the MMA issuer)
+    // by one thread (the even CTA's MMA issuer, the odd CTA's producer)
     auto tq_pop = [&](uint32_t k, unsigned long long &v) {
         const uint32_t slot = k % TQ;
-        if (!mbar_wait(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort)) return false;
+        if (!mbar_wait<true>(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort)) return false;
         v = s_tq[slot];
-        mbar_arrive(b_tqempty + 8 * slot);
+        mbar_arrive_cl(L_tqempty + 8 * slot);  // release (CTA scope) orders the read before the arrival
         return true;
     };
     // by a whole epilogue warp: lane 0 waits, reads and releases the slot, then
@@ -385,10 +519,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int ok = 0;
         if ((threadIdx.x & 31) == 0) {
             const uint32_t slot = k % TQ;
-            ok = mbar_wait(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort) ? 1 : 0;
+            ok = mbar_wait<true>(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort) ? 1 : 0;
             if (ok) {
                 r = s_tq[slot];
-                mbar_arrive(b_tqempty + 8 * slot);
+                mbar_arrive_cl(L_tqempty + 8 * slot);  // release (CTA scope) orders the read before the arrival
             }
         }
         v = __shfl_sync(0xffffffffu, r, 0);
@@ -397,50 +531,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     // The TMA and MMA roles run on lane 0 of their warps.  Between two MMAs
     // the issuing thread does nothing but add descriptor offsets: a
-    // 128x128x16 MMA takes about 68 cycles, and any longer gap in the issue
-    // stream leaves the tensor pipe idle.  Each stage holds one plane of one
-    // 64-wide K chunk of the column block: the MMA thread waits once per
-    // 4 (P - pb) MMAs for column plane pb.
+    // 256x256x16 pair MMA takes about 136 cycles on each SM, and any longer
+    // gap in the issue stream leaves the tensor pipes idle.  Each stage holds
+    // one plane of one 64-wide K chunk of a CTA's column block: the MMA thread
+    // waits once per 4 (P - pb) MMAs for column plane pb.
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer
-        if (lane == 0) {
+        // ------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0 && run) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
             uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, loads = 0, k = 0;
             bool ok = true;
-            // this CTA's up-front run of tile numbers, then runs from the counter
-            uint64_t t = (uint64_t)blockIdx.x * g.static_per, tend = t + g.static_per;
-            while (ok) {
-                if (t >= tend) {
-                    t = g.dyn_start + atomicAdd(g.tile_counter, (unsigned long long)g.chunk);
-                    if (t >= g.ntiles) break;
-                    tend = t + g.chunk < g.ntiles ? t + g.chunk : g.ntiles;
+            // the pair's up-front run of units, then runs from the counter
+            uint64_t u = (uint64_t)(blockIdx.x >> 1) * g.static_per, uend = u + g.static_per;
+            for (;;) {
+                uint32_t R, C;
+                if (leader) {
+                    bool have = false;
+                    while (!have) {
+                        if (u >= uend) {
+                            u = g.dyn_start + atomicAdd(g.tile_counter, (unsigned long long)g.chunk);
+                            if (u >= g.nunits) break;
+                            uend = u + g.chunk < g.nunits ? u + g.chunk : g.nunits;
+                        }
+                        have = unit_of<MAP>(u++, g.mb, R, C);
+                    }
+                    if (!have) break;
+                    if (!tq_push(k++, ((unsigned long long)R << 32) | C)) {
+                        ok = false;
+                        break;
+                    }
+                } else {
+                    unsigned long long v;
+                    if (!tq_pop(k++, v)) {
+                        ok = false;
+                        break;
+                    }
+                    if (v == TQ_END) break;
+                    R = (uint32_t)(v >> 32);
+                    C = (uint32_t)v;
                 }
-                uint32_t bi, bj;
-                if (!tile_of<MAP>(t++, g.m, bi, bj)) continue;
-                if (!tq_push(k++, ((unsigned long long)bi << 32) | bj)) {
-                    ok = false;
-                    break;
-                }
-                if (bi != a_row) {
+                const uint32_t rb = 2 * R + rank, cb = 2 * C + rank;  // this CTA's row and column blocks
+                if (R != a_row) {
                     if (a_loads > 0 && !mbar_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(b_fullA, a_bytes);
+                    if (leader) mbar_expect_tx(b_fullA, 2 * a_bytes);
                     for (uint32_t kc = 0; kc < g.nkc; ++kc)
-                        for (int p = 0; p < P; ++p)
-                            tma_load_3d(sA + (kc * P + p) * CHUNK_BYTES, &tmap, b_fullA, kc * KCH, bi * TILE, p);
+                        for (int pl = 0; pl < P; ++pl)
+                            tma_load_3d_pair(sA + (kc * P + pl) * CHUNK_BYTES, &tmap, L_fullA, kc * KCH, rb * TILE, pl);
                     ++a_loads;
-                    a_row = bi;
+                    a_row = R;
                 }
                 for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
-                    for (int p = 0; p < P; ++p) {
+                    for (int pl = 0; pl < P; ++pl) {
                         if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
                             ok = false;
                             break;
                         }
-                        mbar_expect_tx(b_fullB + 8 * stage, stage_bytes);
-                        tma_load_3d(sB + stage * CHUNK_BYTES, &tmap, b_fullB + 8 * stage, kc * KCH, bj * TILE, p);
+                        if (leader) mbar_expect_tx(b_fullB + 8 * stage, 2 * stage_bytes);
+                        tma_load_3d_pair(sB + stage * CHUNK_BYTES, &tmap, L_fullB + 8 * stage, kc * KCH, cb * TILE, pl);
                         ++loads;
                         if (++stage == g.stages) {
                             stage = 0;
@@ -448,23 +598,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
+                if (!ok) break;
             }
-            if (ok) ok = tq_push(k, TQ_END);
-            if (!ok) {
-                s_abort = 1;
-                atomicExch(g.status, (int)TRI_ETIMEOUT);
+            if (leader && ok) ok = tq_push(k, TQ_END);
+            if (!ok) give_up();
+            // never leave a copy in flight: the even CTA waits for the last
+            // load into every stage (load k went to stage k % stages, in phase
+            // k / stages; the phase completes only once both CTAs' bytes have
+            // landed), and the final cluster barrier holds the odd CTA until then
+            if (leader) {
+                for (uint32_t st = 0; st < g.stages && st < loads; ++st) {
+                    const uint32_t last = loads - 1 - ((loads - 1 - st) % g.stages);
+                    mbar_wait(b_fullB + 8 * st, (last / g.stages) & 1, nullptr);
+                }
+                if (a_loads) mbar_wait(b_fullA, (a_loads - 1) & 1, nullptr);
             }
-            // never leave a copy in flight: wait for the last load into every
-            // stage (load k went to stage k % stages, in phase k / stages)
-            for (uint32_t st = 0; st < g.stages && st < loads; ++st) {
-                const uint32_t last = loads - 1 - ((loads - 1 - st) % g.stages);
-                mbar_wait(b_fullB + 8 * st, (last / g.stages) & 1, nullptr);
-            }
-            if (a_loads) mbar_wait(b_fullA, (a_loads - 1) & 1, nullptr);
         }
     } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        // ------------------------------------------------ MMA issuer (even CTA)
+        if (lane == 0 && leader && run) {
             uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, acc = 0, acc_phase = 0;
             bool ok = true;
             const uint64_t a_desc0 = ((uint64_t)kDescHi << 32) | sdesc_lo(sA);
@@ -477,22 +629,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 if (v == TQ_END) break;
-                const uint32_t bi = (uint32_t)(v >> 32);
-                if (bi != a_row) {
-                    if (a_loads > 0) umma_commit(b_freeA);  // old A is free once issued MMAs finish
+                const uint32_t R = (uint32_t)(v >> 32);
+                if (R != a_row) {
+                    if (a_loads > 0) umma2_commit_both(b_freeA);  // old A is free once issued MMAs finish
                     if (!mbar_wait(b_fullA, a_loads & 1, &s_abort)) {
                         ok = false;
                         break;
                     }
                     ++a_loads;
-                    a_row = bi;
+                    a_row = R;
                 }
                 if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + acc * TILE;
+                const uint32_t d_tmem = tmem + acc * (2 * TILE);  // 256 columns per accumulator
                 for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
                     const uint64_t a_desc = a_desc0 + kc * P * CH16;
 #pragma unroll
@@ -507,11 +659,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         for (int pa = 0; pa + pb < P; ++pa)
 #pragma unroll
                             for (int kk = 0; kk < KCH / 16; ++kk)
-                                // the column tile is the M operand: TMEM lane = output column;
-                                // +2 per 16-element K step (32 bytes in 16-byte units)
-                                umma_bf16(d_tmem, b_desc + 2 * kk, a_desc + pa * CH16 + 2 * kk,
-                                          (kc | pb | pa | kk) ? 1u : 0u);
-                        umma_commit(b_emptyB + 8 * stage);  // stage free when these MMAs finish
+                                // the column blocks are the M operand: TMEM lane = output
+                                // column; +2 per 16-element K step (32 bytes in 16-byte units)
+                                umma2_bf16(d_tmem, b_desc + 2 * kk, a_desc + pa * CH16 + 2 * kk,
+                                           (kc | pb | pa | kk) ? 1u : 0u);
+                        umma2_commit_both(b_emptyB + 8 * stage);  // stage free (both CTAs) when these MMAs finish
                         if (++stage == g.stages) {
                             stage = 0;
                             b_phase ^= 1;
@@ -519,43 +671,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 if (!ok) break;
-                umma_commit(b_tfull + 8 * acc);  // accumulator ready for the epilogue
+                umma2_commit_both(b_tfull + 8 * acc);  // accumulators ready for both epilogues
                 if (++acc == 2) {
                     acc = 0;
                     acc_phase ^= 1;
                 }
             }
-            if (!ok) {
-                s_abort = 1;
-                atomicExch(g.status, (int)TRI_ETIMEOUT);
-            }
+            if (!ok) give_up();
             // all issued MMAs complete before TMEM is released
-            umma_commit(b_done);
+            umma2_commit_own(b_done);
             mbar_wait(b_done, 0, nullptr);
         }
-    } else {
-        // ------------------------------------------------ epilogue (warps 2..17)
-        // The accumulator holds the tile transposed: TMEM lane = output column
-        // j, TMEM column = output row i.  Warp e = warp - 2 reads lane quarter
-        // q = warp % 4 (the quarter a warp may access), so each thread owns one
-        // column j, and takes the 16-row chunks c = grp + NG u (grp = e / 4,
-        // NG = NEPI / 4 warps per quarter) of the tile's 8.  For every row the warp's 32 lanes hold 32
-        // consecutive entries of that packed row: one coalesced 128-byte
-        // store per row, straight from registers.  The next chunk's TMEM load
-        // is in flight while the current one is processed; the next tile's
-        // norms are fetched while the current tile is stored.
+    } else if (run) {
+        // ------------------------------------------------ epilogue (warps 2..17, both CTAs)
+        // The accumulator holds this CTA's two tiles (2R + t, 2C + rank),
+        // t = 0, 1, transposed: TMEM lane = output column j, TMEM column t *
+        // 128 + (row i within the tile).  Warp e = warp - 2 reads lane quarter
+        // q = warp % 4 (the quarter a warp may access), so each thread owns
+        // one column j, and takes the 16-row chunks c = grp + NG u (grp = e /
+        // 4, NG = NEPI / 4 warps per quarter) of each tile's 8.  The next
+        // chunk's TMEM load is in flight while the current one is processed;
+        // the next tile's norms are fetched while the current tile is stored.
+        // A tile above the diagonal (the odd CTA's upper tile of a diagonal
+        // unit) or below the last row block is computed but not read.
         constexpr int NG = NEPI / 4;                // warps per TMEM lane quarter
         constexpr int NCH = TILE / EPI_ROWS / NG;   // 16-row chunks per warp and tile
         const uint32_t e = warp - 2, q = warp & 3, grp = e >> 2;
         float *snorm = epi + e * NORM_FLOATS;     // norms of this warp's rows, two buffers
-        float *stg = stage_base + grp * 2 * STG_FLOATS;  // this row group's two staging buffers
+        float *stg = stage_base + grp * 2 * STG_FLOATS;  // this row group's two staging buffers (P = 2)
         uint32_t hc = 0;                                   // halves staged so far (selects the buffer)
         const float tau = g.tau;
         // next tile's norms: lane l holds the norms of row l % 16 of chunks
         // u = 2v + l / 16 (16 rows each) and of its own column
         float pfr[NCH / 2], pfj = 0.0f;
-        auto prefetch = [&](unsigned long long tv) {
-            const uint32_t a = (uint32_t)(tv >> 32), b = (uint32_t)tv;
+        auto prefetch = [&](uint32_t a, uint32_t b) {  // row block a, column block b
 #pragma unroll
             for (int v = 0; v < NCH / 2; ++v) {
                 const uint32_t u = 2 * v + (lane >> 4);
@@ -567,165 +716,175 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         };
         uint32_t acc = 0, acc_phase = 0, nbuf = 0, k = 0;
         auto fail = [&]() {
-            if (lane == 0) {
-                s_abort = 1;
-                atomicExch(g.status, (int)TRI_ETIMEOUT);
-            }
+            if (lane == 0) give_up();
         };
         unsigned long long cur;
         if (!tq_pop_warp(k++, cur)) {
             fail();
             cur = TQ_END;
         }
-        if (cur != TQ_END) prefetch(cur);
+        if (cur != TQ_END) prefetch(2 * (uint32_t)(cur >> 32), 2 * (uint32_t)cur + rank);
         while (cur != TQ_END) {
-            const uint32_t bi = (uint32_t)(cur >> 32), bj = (uint32_t)cur;
-            float *rn = snorm + nbuf * 32;  // this tile's row norms: [chunk u][16]
-#pragma unroll
-            for (int v = 0; v < NCH / 2; ++v) rn[32 * v + lane] = pfr[v];
-            const float nj = pfj;
-            __syncwarp();
-            unsigned long long nxt;
-            if (!tq_pop_warp(k++, nxt)) {
+            const uint32_t R = (uint32_t)(cur >> 32), bj = 2 * (uint32_t)cur + rank;
+            unsigned long long nxt = TQ_END;
+            bool stop = false;
+            if (!warp_wait<true>(b_tfull + 8 * acc, acc_phase, &s_abort)) {
                 fail();
                 break;
             }
-            if (nxt != TQ_END) prefetch(nxt);
-            if (!warp_wait(b_tfull + 8 * acc, acc_phase, &s_abort)) {
-                if (lane == 0) {
-                    s_abort = 1;
-                    atomicExch(g.status, (int)TRI_ETIMEOUT);
-                }
-                break;
-            }
             tc_fence_after();
-            const uint32_t j = bj * TILE + q * 32 + lane;  // this thread's column
-            const uint32_t taddr = tmem + ((q * 32) << 16) + acc * TILE;
-            uint32_t raw[2][EPI_ROWS];
-            tmem_ld16(taddr + grp * EPI_ROWS, raw[0]);
+#pragma unroll 1
+            for (uint32_t t = 0; t < 2; ++t) {
+                const uint32_t bi = 2 * R + t;
+                const bool valid = bj <= bi && bi < g.m;
+                float *rn = snorm + nbuf * 32;  // this tile's row norms: [chunk u][16]
 #pragma unroll
-            for (int u = 0; u < NCH; ++u) {
-                uint32_t(&cur)[EPI_ROWS] = raw[u & 1];
-                tmem_wait16(cur);
-                if (u + 1 < NCH) tmem_ld16(taddr + (grp + NG * (u + 1)) * EPI_ROWS, raw[(u + 1) & 1]);
-                const uint32_t i0 = bi * TILE + (grp + NG * u) * EPI_ROWS;  // first row of the chunk
-                float ni[EPI_ROWS];
-#pragma unroll
-                for (int k = 0; k < EPI_ROWS; k += 4) {
-                    const float4 v4 = *reinterpret_cast<const float4 *>(rn + u * EPI_ROWS + k);
-                    ni[k] = v4.x;
-                    ni[k + 1] = v4.y;
-                    ni[k + 2] = v4.z;
-                    ni[k + 3] = v4.w;
+                for (int v = 0; v < NCH / 2; ++v) rn[32 * v + lane] = pfr[v];
+                const float nj = pfj;
+                __syncwarp();
+                if (t == 0) {
+                    prefetch(bi + 1, bj);
+                } else if (!tq_pop_warp(k++, nxt)) {
+                    fail();
+                    stop = true;
+                    nxt = TQ_END;
+                } else if (nxt != TQ_END) {
+                    prefetch(2 * (uint32_t)(nxt >> 32), 2 * (uint32_t)nxt + rank);
                 }
-                // fast path: d = d2 * rsqrt(d2); one test per chunk for a pair
-                // with d2 <= tau (|x_i|^2 + |x_j|^2) (cancellation, the
-                // diagonal, or padding)
-                float dv[EPI_ROWS], d2v[EPI_ROWS];
-                float worst = 1.0f;
+                if (valid) {
+                    const uint32_t j = bj * TILE + q * 32 + lane;  // this thread's column
+                    const uint32_t taddr = tmem + ((q * 32) << 16) + acc * (2 * TILE) + t * TILE;
+                    uint32_t raw[2][EPI_ROWS];
+                    tmem_ld16(taddr + grp * EPI_ROWS, raw[0]);
 #pragma unroll
-                for (int k = 0; k < EPI_ROWS; ++k) {
-                    const float s = ni[k] + nj;
-                    const float d2 = fmaf(-2.0f, __uint_as_float(cur[k]), s);
-                    d2v[k] = d2;
-                    worst = fminf(worst, fmaf(-tau, s, d2));
-                    dv[k] = d2 * rsqrt_approx(d2);
-                }
-                if (worst <= 0.0f) {
+                    for (int u = 0; u < NCH; ++u) {
+                        uint32_t(&cur)[EPI_ROWS] = raw[u & 1];
+                        tmem_wait16(cur);
+                        if (u + 1 < NCH) tmem_ld16(taddr + (grp + NG * (u + 1)) * EPI_ROWS, raw[(u + 1) & 1]);
+                        const uint32_t i0 = bi * TILE + (grp + NG * u) * EPI_ROWS;  // first row of the chunk
+                        float ni[EPI_ROWS];
 #pragma unroll
-                    for (int k = 0; k < EPI_ROWS; ++k) {
-                        const float d2 = d2v[k];
-                        if (d2 <= tau * (ni[k] + nj)) {
-                            const uint32_t i = i0 + k;
-                            if (i < g.n && j < i) {
-                                const unsigned long long slot = atomicAdd(g.flag_count, 1ull);
-                                if (slot < g.flag_cap) g.flag_list[slot] = ((unsigned long long)i << 32) | j;
+                        for (int k = 0; k < EPI_ROWS; k += 4) {
+                            const float4 v4 = *reinterpret_cast<const float4 *>(rn + u * EPI_ROWS + k);
+                            ni[k] = v4.x;
+                            ni[k + 1] = v4.y;
+                            ni[k + 2] = v4.z;
+                            ni[k + 3] = v4.w;
+                        }
+                        // fast path: d = d2 * rsqrt(d2); one test per chunk for a pair
+                        // with d2 <= tau (|x_i|^2 + |x_j|^2) (cancellation, the
+                        // diagonal, or padding)
+                        float dv[EPI_ROWS], d2v[EPI_ROWS];
+                        float worst = 1.0f;
+#pragma unroll
+                        for (int k = 0; k < EPI_ROWS; ++k) {
+                            const float s = ni[k] + nj;
+                            const float d2 = fmaf(-2.0f, __uint_as_float(cur[k]), s);
+                            d2v[k] = d2;
+                            worst = fminf(worst, fmaf(-tau, s, d2));
+                            dv[k] = d2 * rsqrt_approx(d2);
+                        }
+                        if (worst <= 0.0f) {
+#pragma unroll
+                            for (int k = 0; k < EPI_ROWS; ++k) {
+                                const float d2 = d2v[k];
+                                if (d2 <= tau * (ni[k] + nj)) {
+                                    const uint32_t i = i0 + k;
+                                    if (i < g.n && j < i) {
+                                        const unsigned long long slot = atomicAdd(g.flag_count, 1ull);
+                                        if (slot < g.flag_cap) g.flag_list[slot] = ((unsigned long long)i << 32) | j;
+                                    }
+                                    // provisional value (flagged pairs are recomputed; the diagonal is exact 0)
+                                    dv[k] = (i == j || d2 <= 0.0f) ? 0.0f : d2 * rsqrt_approx(d2);
+                                }
                             }
-                            // provisional value (flagged pairs are recomputed; the diagonal is exact 0)
-                            dv[k] = (i == j || d2 <= 0.0f) ? 0.0f : d2 * rsqrt_approx(d2);
+                        }
+                        if constexpr (P == 2) {
+                        // Store through shared memory in two halves of 8 rows: the row
+                        // group's four warps (one per 32-column quarter) write their
+                        // columns of each row into a staging row shifted by the row's
+                        // 16-byte phase (T2(i0 + k) mod 4, which depends on k only since
+                        // i0 is a multiple of 16); then each warp writes two whole row
+                        // segments, the aligned middle with one float4 per lane and the
+                        // ends with scalar stores, so every 128-byte line of a segment's
+                        // middle is written by one instruction.  The two staging buffers
+                        // alternate: the barrier before a half's stores also tells each
+                        // warp that the group has finished reading the buffer it will
+                        // fill next, so one barrier per half suffices.
+#pragma unroll
+                        for (int half = 0; half < EPI_ROWS / STG_ROWS; ++half) {
+                            float *sb = stg + (hc & 1) * STG_FLOATS;
+                            ++hc;
+#pragma unroll
+                            for (int kk = 0; kk < STG_ROWS; ++kk) {
+                                const int k = half * STG_ROWS + kk;
+                                sb[kk * STG_LD + row_phase(k) + q * 32 + lane] = dv[k];
+                            }
+                            named_sync(1 + grp, 128);
+#pragma unroll
+                            for (int r2 = 0; r2 < STG_ROWS / 4; ++r2) {
+                                const uint32_t kk = q * (STG_ROWS / 4) + r2, k = half * STG_ROWS + kk, i = i0 + k;
+                                if (i < g.n) {
+                                    const uint32_t len = bi == bj ? i - bj * TILE + 1 : TILE;  // columns of row i here
+                                    float *seg = g.out + T2(i) + bj * TILE;
+                                    const uint32_t ph = row_phase(k), head = (4 - ph) & 3;
+                                    const float *src = sb + kk * STG_LD + ph;
+                                    const uint32_t h = head < len ? head : len;
+                                    const uint32_t nv = (len - h) >> 2;
+                                    if (lane < nv)
+                                        __stcs(reinterpret_cast<float4 *>(seg + h) + lane,
+                                               *reinterpret_cast<const float4 *>(src + h + 4 * lane));
+                                    const uint32_t t0 = h + 4 * nv, tail = len - t0;  // h <= 3, tail <= 3
+                                    if (lane < h) __stcs(seg + lane, src[lane]);
+                                    if (lane >= 4 && lane - 4 < tail) __stcs(seg + t0 + lane - 4, src[t0 + lane - 4]);
+                                }
+                            }
+                        }
+                        } else {
+                            // Direct stores: for each row the warp's 32 lanes hold 32
+                            // consecutive packed entries, written by one 128-byte store.
+                            // For P = 3 the tensor core's operand reads already take most
+                            // of the shared-memory bandwidth, and staging (which also
+                            // costs two operand stages) measured slower.
+                            float *row = g.out + T2(i0) + j;  // row i0, column j
+                            if (bi != bj && (bi + 1) * TILE <= g.n) {
+#pragma unroll
+                                for (int k = 0; k < EPI_ROWS; ++k) {
+                                    __stcs(row, dv[k]);
+                                    row += i0 + k + 1;  // T2(i + 1) - T2(i)
+                                }
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < EPI_ROWS; ++k) {
+                                    const uint32_t i = i0 + k;
+                                    if (i < g.n && j <= i) __stcs(row, dv[k]);
+                                    row += i + 1;
+                                }
+                            }
                         }
                     }
                 }
-                if constexpr (P == 2) {
-                // Store through shared memory in two halves of 8 rows: the row
-                // group's four warps (one per 32-column quarter) write their
-                // columns of each row into a staging row shifted by the row's
-                // 16-byte phase (T2(i0 + k) mod 4, which depends on k only since
-                // i0 is a multiple of 16); then each warp writes two whole row
-                // segments, the aligned middle with one float4 per lane and the
-                // ends with scalar stores, so every 128-byte line of a segment's
-                // middle is written by one instruction.  The two staging buffers
-                // alternate: the barrier before a half's stores also tells each
-                // warp that the group has finished reading the buffer it will
-                // fill next, so one barrier per half suffices.
-#pragma unroll
-                for (int half = 0; half < EPI_ROWS / STG_ROWS; ++half) {
-                    float *sb = stg + (hc & 1) * STG_FLOATS;
-                    ++hc;
-#pragma unroll
-                    for (int kk = 0; kk < STG_ROWS; ++kk) {
-                        const int k = half * STG_ROWS + kk;
-                        sb[kk * STG_LD + row_phase(k) + q * 32 + lane] = dv[k];
-                    }
-                    named_sync(1 + grp, 128);
-#pragma unroll
-                    for (int r2 = 0; r2 < STG_ROWS / 4; ++r2) {
-                        const uint32_t kk = q * (STG_ROWS / 4) + r2, k = half * STG_ROWS + kk, i = i0 + k;
-                        if (i < g.n) {
-                            const uint32_t len = bi == bj ? i - bj * TILE + 1 : TILE;  // columns of row i here
-                            float *seg = g.out + T2(i) + bj * TILE;
-                            const uint32_t ph = row_phase(k), head = (4 - ph) & 3;
-                            const float *src = sb + kk * STG_LD + ph;
-                            const uint32_t h = head < len ? head : len;
-                            const uint32_t nv = (len - h) >> 2;
-                            if (lane < nv)
-                                __stcs(reinterpret_cast<float4 *>(seg + h) + lane,
-                                       *reinterpret_cast<const float4 *>(src + h + 4 * lane));
-                            const uint32_t t0 = h + 4 * nv, tail = len - t0;  // h <= 3, tail <= 3
-                            if (lane < h) __stcs(seg + lane, src[lane]);
-                            if (lane >= 4 && lane - 4 < tail) __stcs(seg + t0 + lane - 4, src[t0 + lane - 4]);
-                        }
-                    }
-                }
-                } else {
-                    // Direct stores: for each row the warp's 32 lanes hold 32
-                    // consecutive packed entries, written by one 128-byte store.
-                    // For P = 3 the tensor core's operand reads already take most
-                    // of the shared-memory bandwidth, and staging (which also
-                    // costs two operand stages) measured slower.
-                    float *row = g.out + T2(i0) + j;  // row i0, column j
-                    if (bi != bj && (bi + 1) * TILE <= g.n) {
-#pragma unroll
-                        for (int k = 0; k < EPI_ROWS; ++k) {
-                            __stcs(row, dv[k]);
-                            row += i0 + k + 1;  // T2(i + 1) - T2(i)
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < EPI_ROWS; ++k) {
-                            const uint32_t i = i0 + k;
-                            if (i < g.n && j <= i) __stcs(row, dv[k]);
-                            row += i + 1;
-                        }
-                    }
-                }
+                nbuf ^= 1;
             }
             tc_fence_before();
-            if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
+            if (lane == 0) mbar_arrive_cl(L_tempty + 8 * acc);
             if (++acc == 2) {
                 acc = 0;
                 acc_phase ^= 1;
             }
-            nbuf ^= 1;
+            if (stop) break;
             cur = nxt;
         }
     }
+    // neither CTA releases its TMEM or exits while the other (or the even
+    // CTA's MMAs and copies) may still use its shared memory or accumulators
     tc_fence_before();
     __syncthreads();
+    cluster_sync();
     tc_fence_after();
     if (warp == 1) {
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -809,11 +968,46 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.nkc = p.dp / KCH;
     const size_t stg = p.P == 2 ? (size_t)(NEPI / 4) * 2 * STG_FLOATS : 0;  // P = 2 stages its stores
     const size_t fixed = 1024 /*align*/ + (NEPI * NORM_FLOATS + stg) * 4 + 8 * (7 + 2 * MAX_STAGES);
-    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;
+    const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;  // one row block per CTA
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
     p.stages = (uint32_t)std::min<size_t>(MAX_STAGES, (SMEM_LIMIT - fixed - a) / st);
     p.smem = fixed + a + p.stages * st;
     return true;
+}
+
+// Launches the pair kernel on as many CTA pairs as can be resident at once
+// (cached per instantiation and shared-memory size), splitting the units into
+// an up-front run per pair and counter-driven runs.
+template <int MP, int PP>
+cudaError_t launch_gram(const CUtensorMap &tmap, GramArgs g, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(gram_kernel<MP, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    static int cached_dev = -1, cached_pairs = 0;
+    static size_t cached_smem = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cached_dev != dev || cached_smem != smem) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * (num_sms() / 2));
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, gram_kernel<MP, PP>, &cfg) != cudaSuccess || ncl < 1) {
+            (void)cudaGetLastError();
+            ncl = (int)(num_sms() / 2);
+        }
+        cached_dev = dev;
+        cached_smem = smem;
+        cached_pairs = ncl;
+    }
+    const uint64_t pairs = std::min<uint64_t>((uint64_t)(cached_pairs > 0 ? cached_pairs : 1), g.nunits);
+    g.static_per = g.nunits * STATIC_PCT / 100 / pairs;
+    g.dyn_start = g.static_per * pairs;
+    g.chunk = DYN_CHUNK;
+    gram_kernel<MP, PP><<<(unsigned)(2 * pairs), NTHREADS, smem, s>>>(tmap, g);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -857,12 +1051,13 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     if (!plan(d, prec, pl)) return TRI_ERANGE;
     const WsLayout L = ws_layout(n, d, prec);
     if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
-    const uint32_t m = (n + TILE - 1) / TILE;
-    const uint64_t ntiles = map == TRI_MAP_LAMBDA ? T2(m) : (uint64_t)m * m;
-    if (ntiles > 0xFFFFFFFFull) return TRI_ERANGE;
+    const uint32_t m = (n + TILE - 1) / TILE, mb = (m + 1) / 2;
+    // units: 2 x 2 tile blocks, lambda over the mb-row triangle or the mb x mb box
+    const uint64_t nunits = map == TRI_MAP_LAMBDA ? T2(mb) : (uint64_t)mb * mb;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return TRI_ECUDA;
     char *ws = (char *)workspace;
+    // 128-row blocks of the planes (row blocks and column blocks alike)
     CUtensorMap tmap;
     const cuuint64_t gdim[3] = {pl.dp, n, (cuuint64_t)pl.P};
     const cuuint64_t gstride[2] = {(cuuint64_t)pl.dp * 2, (cuuint64_t)n * pl.dp * 2};
@@ -876,7 +1071,8 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     g.n = n;
     g.nkc = pl.nkc;
     g.m = m;
-    g.ntiles = ntiles;
+    g.mb = mb;
+    g.nunits = nunits;
     g.stages = pl.stages;
     g.tau = pl.P == 3 ? TAU_X6 : TAU_X3;
     g.norms = (const float *)(ws + L.norms);
@@ -886,32 +1082,14 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     g.tile_counter = (unsigned long long *)(ws + L.hdr + 16);
     g.flag_list = (unsigned long long *)(ws + L.flags);
     g.flag_cap = L.cap;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(num_sms(), ntiles);
-    g.static_per = ntiles * STATIC_PCT / 100 / grid;
-    g.dyn_start = g.static_per * grid;
-    g.chunk = DYN_CHUNK;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(g.tile_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return TRI_ECUDA;
     cudaError_t e;
-#define TRI_G(MP, PP)                                                                                          \
-    e = cudaFuncSetAttribute(gram_kernel<MP, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);  \
-    if (e == cudaSuccess) gram_kernel<MP, PP><<<grid, NTHREADS, pl.smem, s>>>(tmap, g);
-    if (map == TRI_MAP_LAMBDA) {
-        if (pl.P == 3) {
-            TRI_G(MAP_LAMBDA, 3)
-        } else {
-            TRI_G(MAP_LAMBDA, 2)
-        }
-    } else {
-        if (pl.P == 3) {
-            TRI_G(MAP_BB, 3)
-        } else {
-            TRI_G(MAP_BB, 2)
-        }
-    }
-#undef TRI_G
-    if (e != cudaSuccess) return TRI_ECUDA;
-    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+    if (map == TRI_MAP_LAMBDA)
+        e = pl.P == 3 ? launch_gram<MAP_LAMBDA, 3>(tmap, g, pl.smem, s) : launch_gram<MAP_LAMBDA, 2>(tmap, g, pl.smem, s);
+    else
+        e = pl.P == 3 ? launch_gram<MAP_BB, 3>(tmap, g, pl.smem, s) : launch_gram<MAP_BB, 2>(tmap, g, pl.smem, s);
+    return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
 
 extern "C" int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out, int prec, void *workspace,
