@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 # summarised in profiles/gram_kernel_lambda_bf16x6_n65536_d128.md (taken at
 # N = 16384 and scaled by the number of pairs).  Keyed by (prec, n, d); a
 # kernel change makes the figure stale, and it is then removed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("bf16x6", 65536, 128): 8.064e9}
 
 
 def load_peaks():
@@ -500,9 +500,12 @@ def main():
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "bf16x6": "bf16"}[args.prec],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP, "map": "lambda",
-                   "tile": "16x16 threads x 4x4 pairs" if prec == tri.FP32 else "128x128 tcgen05 tiles",
+                   "tile": ("16x16 threads x 4x4 pairs" if prec == tri.FP32
+                            else "2x2 blocks of 128x128 tiles per CTA pair (tcgen05.mma.cta_group::2, M=N=256)"),
                    "prec": args.prec, "pairs_per_step": P,
-                   "l2": "each step writes the 8.59 GB triangle (> 129 MB L2), which flushes L2 between steps"},
+                   "l2": (f"each step writes the {4 * P / 1e9:.2f} GB triangle (> 129 MB L2), which flushes L2 "
+                          "between steps" if 4 * P > 129e6 else
+                          f"the {4 * P / 1e6:.1f} MB triangle fits in L2: no flush between steps")},
         "bb": {"ms_per_step": ms_bb, "value": world * P / (ms_bb * 1e-3), "I_bb_over_lambda": ms_bb / ms_step},
         "fp32_lambda": {"ms_per_step": ms_fp32, "value": world * P / (ms_fp32 * 1e-3),
                         "speedup_of_headline": ms_fp32 / ms_step},
