@@ -187,6 +187,29 @@ TRI_API int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out, in
                           size_t ws_bytes, unsigned long long *n_flagged, void *stream);
 
 /*
+ * End-to-end EDM from and to host memory (not in the paper, which starts
+ * from device-resident points): copies x_host (n x d FP32, row-major) to
+ * x_dev, runs tri_edm_prepare, then computes the packed triangle in `bands`
+ * row bands (Gram term + FP64 recompute of the band's flagged pairs) and
+ * copies each finished band from out_dev to out_host on a library-owned
+ * copy stream while the next band computes, so the device-to-host copy (the
+ * bound of this call on a host attached through NVLink-C2C) overlaps the
+ * compute.  bands = 0 picks about 512 MB of output per band (1 to 16).
+ * prec: TRI_BF16X3 or TRI_BF16X6; map: TRI_MAP_LAMBDA or TRI_MAP_BB.
+ * x_dev (n*d floats), out_dev (n(n+1)/2 floats, 16-byte aligned) and the
+ * workspace (tri_edm_workspace_size bytes, 256-byte aligned) are device
+ * buffers owned by the caller.  Host buffers should be pinned for the copies
+ * to run asynchronously.  The call enqueues the work and returns: `stream`
+ * completes after the last copy, so synchronise it before reading out_host.
+ * out_host and out_dev hold the same triangle as tri_edm's out.
+ * Errors: TRI_EINVAL (null pointer, zero size, bad map or prec, unaligned
+ * out_dev), TRI_ERANGE / TRI_ENOSPACE as tri_edm, TRI_ECUDA.
+ */
+TRI_API int tri_edm_host(const float *x_host, uint32_t n, uint32_t d, float *out_host, int map, int prec,
+                         uint32_t bands, float *x_dev, float *out_dev, void *workspace, size_t ws_bytes,
+                         unsigned long long *n_flagged, void *stream);
+
+/*
  * tri_edm_batched -- many EDM triangles of uneven size in one persistent
  * launch (lambda applied to each instance's own block numbers, found from
  * an exclusive prefix sum of the per-instance block counts m_k(m_k+1)/2).

@@ -37,6 +37,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 
 #include "tri_internal.h"
 #include "tri_maps.cuh"
@@ -345,7 +347,7 @@ struct GramArgs {
     uint32_t n, nkc;           // points, 64-wide K chunks
     uint32_t m;                // tile rows of the triangle
     uint32_t mb;               // unit rows: ceil(m / 2)
-    uint64_t nunits;           // units walked: lambda over the mb-row triangle or the mb x mb box
+    uint64_t u0, nunits;       // units walked: [u0, nunits) of lambda over the mb-row triangle or the mb x mb box
     uint64_t static_per;       // units per CTA pair in its up-front run
     uint64_t dyn_start;        // first unit handed out by the counter
     uint32_t chunk;            // units per grab from the counter
@@ -542,7 +544,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             uint32_t a_row = 0xFFFFFFFFu, a_loads = 0, stage = 0, b_phase = 0, loads = 0, k = 0;
             bool ok = true;
             // the pair's up-front run of units, then runs from the counter
-            uint64_t u = (uint64_t)(blockIdx.x >> 1) * g.static_per, uend = u + g.static_per;
+            uint64_t u = g.u0 + (uint64_t)(blockIdx.x >> 1) * g.static_per, uend = u + g.static_per;
             for (;;) {
                 uint32_t R, C;
                 if (leader) {
@@ -889,17 +891,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 }
 
 // -------------------------------------------------------------- fixup ----
-// FP64 direct-difference recompute of the flagged pairs.  If the list
-// overflowed, every pair whose stored distance passes a slightly wider
-// version of the flag test is recomputed instead.
-__global__ void fixup_kernel(const float *__restrict__ x, uint32_t n, uint32_t d, float *__restrict__ out,
+// FP64 direct-difference recompute of the flagged pairs appended since the
+// previous call (list entries [*start, count); all of them when start is
+// null).  If the list overflowed, every pair of the packed range [p_begin,
+// p_end) whose stored distance passes a slightly wider version of the flag
+// test is recomputed instead.  next_start (if not null) receives the count,
+// for the next call.
+__global__ void fixup_kernel(const float *__restrict__ x, uint32_t d, float *__restrict__ out,
                              const float *__restrict__ norms, const unsigned long long *__restrict__ count,
                              const unsigned long long *__restrict__ list, unsigned long long cap, float tau,
-                             unsigned long long *n_flagged)
+                             unsigned long long *n_flagged, const unsigned long long *start,
+                             unsigned long long *next_start, uint64_t p_begin, uint64_t p_end)
 {
-    const unsigned long long cnt = *count;
+    const unsigned long long cnt = *count, first = start ? *start : 0ull;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (uint64_t)gridDim.x * blockDim.x;
     if (tid == 0 && n_flagged) *n_flagged = cnt;
+    if (tid == 0 && next_start) *next_start = cnt;
     auto recompute = [&](uint32_t i, uint32_t j) {
         const float *xi = x + (size_t)i * d, *xj = x + (size_t)j * d;
         double s = 0.0;
@@ -910,14 +917,13 @@ __global__ void fixup_kernel(const float *__restrict__ x, uint32_t n, uint32_t d
         out[T2(i) + j] = (float)sqrt(s);
     };
     if (cnt <= cap) {
-        for (uint64_t e = tid; e < cnt; e += nth) {
+        for (uint64_t e = first + tid; e < cnt; e += nth) {
             const unsigned long long v = list[e];
             recompute((uint32_t)(v >> 32), (uint32_t)(v & 0xFFFFFFFFu));
         }
     } else {
-        const uint64_t total = T2(n);
         const float wide = 1.0625f * tau;
-        for (uint64_t p = tid; p < total; p += nth) {
+        for (uint64_t p = p_begin + tid; p < p_end; p += nth) {
             uint32_t i, j;
             lambda_diag<TRI_SQRT_X>((uint32_t)p, i, j);
             if (i == j) continue;
@@ -1002,9 +1008,10 @@ cudaError_t launch_gram(const CUtensorMap &tmap, GramArgs g, size_t smem, cudaSt
         cached_smem = smem;
         cached_pairs = ncl;
     }
-    const uint64_t pairs = std::min<uint64_t>((uint64_t)(cached_pairs > 0 ? cached_pairs : 1), g.nunits);
-    g.static_per = g.nunits * STATIC_PCT / 100 / pairs;
-    g.dyn_start = g.static_per * pairs;
+    const uint64_t units = g.nunits - g.u0;
+    const uint64_t pairs = std::min<uint64_t>((uint64_t)(cached_pairs > 0 ? cached_pairs : 1), units);
+    g.static_per = units * STATIC_PCT / 100 / pairs;
+    g.dyn_start = g.u0 + g.static_per * pairs;
     g.chunk = DYN_CHUNK;
     gram_kernel<MP, PP><<<(unsigned)(2 * pairs), NTHREADS, smem, s>>>(tmap, g);
     return cudaGetLastError();
@@ -1039,8 +1046,12 @@ extern "C" int tri_edm_prepare(const float *x, uint32_t n, uint32_t d, int prec,
     return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
 
-extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int prec, void *workspace, size_t ws_bytes,
-                            void *stream)
+namespace {
+
+// Unit rows [R0, R1) of the Gram kernel, whose output is the packed rows
+// [256 R0, min(n, 256 R1)).
+int gram_range(uint32_t n, uint32_t d, float *out, int map, int prec, void *workspace, size_t ws_bytes, uint32_t R0,
+               uint32_t R1, cudaStream_t s)
 {
     if (!out || n == 0 || d == 0) return TRI_EINVAL;
     if (n > TC_MAX_N) return TRI_ERANGE;
@@ -1052,8 +1063,11 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     const WsLayout L = ws_layout(n, d, prec);
     if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
     const uint32_t m = (n + TILE - 1) / TILE, mb = (m + 1) / 2;
+    if (R1 > mb) R1 = mb;
+    if (R0 >= R1) return TRI_OK;
     // units: 2 x 2 tile blocks, lambda over the mb-row triangle or the mb x mb box
-    const uint64_t nunits = map == TRI_MAP_LAMBDA ? T2(mb) : (uint64_t)mb * mb;
+    const uint64_t u0 = map == TRI_MAP_LAMBDA ? T2(R0) : (uint64_t)R0 * mb;
+    const uint64_t nunits = map == TRI_MAP_LAMBDA ? T2(R1) : (uint64_t)R1 * mb;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return TRI_ECUDA;
     char *ws = (char *)workspace;
@@ -1072,6 +1086,7 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     g.nkc = pl.nkc;
     g.m = m;
     g.mb = mb;
+    g.u0 = u0;
     g.nunits = nunits;
     g.stages = pl.stages;
     g.tau = pl.P == 3 ? TAU_X6 : TAU_X3;
@@ -1082,7 +1097,6 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     g.tile_counter = (unsigned long long *)(ws + L.hdr + 16);
     g.flag_list = (unsigned long long *)(ws + L.flags);
     g.flag_cap = L.cap;
-    cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(g.tile_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return TRI_ECUDA;
     cudaError_t e;
     if (map == TRI_MAP_LAMBDA)
@@ -1090,6 +1104,16 @@ extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int pre
     else
         e = pl.P == 3 ? launch_gram<MAP_BB, 3>(tmap, g, pl.smem, s) : launch_gram<MAP_BB, 2>(tmap, g, pl.smem, s);
     return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int tri_edm_gram(uint32_t n, uint32_t d, float *out, int map, int prec, void *workspace, size_t ws_bytes,
+                            void *stream)
+{
+    if (n == 0) return TRI_EINVAL;
+    const uint32_t mb = ((n + TILE - 1) / TILE + 1) / 2;
+    return gram_range(n, d, out, map, prec, workspace, ws_bytes, 0, mb, (cudaStream_t)stream);
 }
 
 extern "C" int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out, int prec, void *workspace,
@@ -1102,10 +1126,11 @@ extern "C" int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out,
     if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
     char *ws = (char *)workspace;
     cudaStream_t s = (cudaStream_t)stream;
-    fixup_kernel<<<num_sms() * 4, 256, 0, s>>>(x, n, d, out, (const float *)(ws + L.norms),
+    fixup_kernel<<<num_sms() * 4, 256, 0, s>>>(x, d, out, (const float *)(ws + L.norms),
                                                (const unsigned long long *)(ws + L.hdr),
                                                (const unsigned long long *)(ws + L.flags), L.cap,
-                                               prec == TRI_BF16X6 ? TAU_X6 : TAU_X3, n_flagged);
+                                               prec == TRI_BF16X6 ? TAU_X6 : TAU_X3, n_flagged, nullptr, nullptr, 0,
+                                               T2(n));
     return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
 
@@ -1116,4 +1141,81 @@ int trihost::edm_tc(const float *x, uint32_t n, uint32_t d, float *out, int map,
     if (st == TRI_OK) st = tri_edm_gram(n, d, out, map, prec, ws, ws_bytes, s);
     if (st == TRI_OK) st = tri_edm_fixup(x, n, d, out, prec, ws, ws_bytes, n_flagged, s);
     return st;
+}
+
+// ---------------------------------------------------------------- host ----
+namespace {
+
+// One non-blocking copy stream per device for tri_edm_host's device-to-host copies.
+cudaStream_t copy_stream()
+{
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+        streams[dev] = nullptr;
+    return streams[dev];
+}
+
+}  // namespace
+
+extern "C" int tri_edm_host(const float *x_host, uint32_t n, uint32_t d, float *out_host, int map, int prec,
+                            uint32_t bands, float *x_dev, float *out_dev, void *workspace, size_t ws_bytes,
+                            unsigned long long *n_flagged, void *stream)
+{
+    if (!x_host || !out_host || !x_dev || !out_dev || n == 0 || d == 0) return TRI_EINVAL;
+    if (prec != TRI_BF16X3 && prec != TRI_BF16X6) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    if (n > TC_MAX_N) return TRI_ERANGE;
+    TcPlan pl;
+    if (!plan(d, prec, pl)) return TRI_ERANGE;
+    const WsLayout L = ws_layout(n, d, prec);
+    if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
+    if ((uintptr_t)out_dev & 15) return TRI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream, cs = copy_stream();
+    if (!cs) return TRI_ECUDA;
+    const uint32_t m = (n + TILE - 1) / TILE, mb = (m + 1) / 2;
+    const uint64_t total = T2(n);
+    // bands of about 512 MB of output each (equal areas: unit-row edges ~ mb sqrt(k / B))
+    if (bands == 0) bands = (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, total * 4 / (512ull << 20)));
+    bands = std::min(bands, mb);
+    char *ws = (char *)workspace;
+    unsigned long long *slot = (unsigned long long *)(ws + L.hdr + 24);  // two list-start slots
+    if (cudaMemcpyAsync(x_dev, x_host, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return TRI_ECUDA;
+    int r = tri_edm_prepare(x_dev, n, d, prec, workspace, ws_bytes, s);  // also zeroes both slots
+    if (r != TRI_OK) return r;
+    uint32_t R0 = 0;
+    for (uint32_t b = 0; b < bands; ++b) {
+        uint32_t R1 = b + 1 == bands ? mb : (uint32_t)std::ceil(mb * std::sqrt((double)(b + 1) / bands));
+        R1 = std::min(std::max(R1, R0 + 1), mb);
+        if (R0 >= mb) break;
+        if ((r = gram_range(n, d, out_dev, map, prec, workspace, ws_bytes, R0, R1, s)) != TRI_OK) return r;
+        const uint64_t p0 = T2(std::min<uint64_t>(n, 2ull * TILE * R0)), p1 = T2(std::min<uint64_t>(n, 2ull * TILE * R1));
+        fixup_kernel<<<num_sms() * 4, 256, 0, s>>>(x_dev, d, out_dev, (const float *)(ws + L.norms),
+                                                   (const unsigned long long *)(ws + L.hdr),
+                                                   (const unsigned long long *)(ws + L.flags), L.cap,
+                                                   prec == TRI_BF16X6 ? TAU_X6 : TAU_X3, n_flagged, slot + (b & 1),
+                                                   slot + ((b + 1) & 1), p0, p1);
+        if (cudaGetLastError() != cudaSuccess) return TRI_ECUDA;
+        // the band's rows are final: copy them while the next band computes
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return TRI_ECUDA;
+        cudaError_t e = cudaEventRecord(ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+        cudaEventDestroy(ev);
+        if (e == cudaSuccess && p1 > p0)
+            e = cudaMemcpyAsync(out_host + p0, out_dev + p0, (p1 - p0) * sizeof(float), cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return TRI_ECUDA;
+        R0 = R1;
+    }
+    // the caller's stream completes only after the last copy
+    cudaEvent_t done;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) return TRI_ECUDA;
+    cudaError_t e = cudaEventRecord(done, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done, 0);
+    cudaEventDestroy(done);
+    return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }

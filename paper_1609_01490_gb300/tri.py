@@ -48,6 +48,7 @@ _SIGS = {
     "tri_edm_prepare": ([_vp, _u32, _u32, _i32, _vp, _sz, _vp], _i32),
     "tri_edm_gram": ([_u32, _u32, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
     "tri_edm_fixup": ([_vp, _u32, _u32, _vp, _i32, _vp, _sz, _vp, _vp], _i32),
+    "tri_edm_host": ([_vp, _u32, _u32, _vp, _i32, _i32, _u32, _vp, _vp, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_batched": ([_vp, _vp, _vp, _u32, _u32, _vp, _vp, _u32, _u32, _vp, _sz, _vp], _i32),
     "tri_edm_batched_workspace_size": ([_u32, _szp], _i32),
     "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
@@ -86,6 +87,13 @@ def _ptr(t) -> int | None:
         return None
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def _hptr(t) -> int:
+    """Pointer of a contiguous host (CPU) tensor; pinned memory keeps the copies asynchronous."""
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
     return t.data_ptr()
 
 
@@ -132,6 +140,17 @@ def tri_edm(x, out, map: int = MAP_LAMBDA, rho: int = 16, reg: int = 0, prec: in
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("tri_edm", _lib.tri_edm(_ptr(x), n, d, _ptr(out), map, rho, reg, prec, _ptr(workspace), ws_bytes,
                                    _ptr(n_flagged), _stream(stream)))
+
+
+def tri_edm_host(x_host, out_host, x_dev, out_dev, workspace, map: int = MAP_LAMBDA, prec: int = BF16X6,
+                 bands: int = 0, n_flagged=None, stream=None) -> None:
+    """Host buffers in and out (pinned CPU tensors), device buffers and workspace
+    supplied by the caller; the call enqueues the work on `stream`."""
+    n, d = x_host.shape
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("tri_edm_host", _lib.tri_edm_host(_hptr(x_host), n, d, _hptr(out_host), map, prec, bands, _ptr(x_dev),
+                                             _ptr(out_dev), _ptr(workspace), ws_bytes, _ptr(n_flagged),
+                                             _stream(stream)))
 
 
 def _nbytes(t) -> int:

@@ -136,3 +136,65 @@ def test_tc_phases_and_errors():
     t.tri_edm_fixup(x, b, t.BF16X6, ws)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("bands", [0, 1, 5])
+def test_tc_edm_host_matches_device_path(bands):
+    # host buffers in and out, banded compute overlapped with the copies: the
+    # same bytes as tri_edm on device buffers, flags included
+    import torch
+    t = tri()
+    D = dev()
+    n, d = 3000, 64
+    x = inputs.edm_normal_points(n, d, seed=77, dup_frac=0.02)
+    size = n * (n + 1) // 2
+    for prec in (t.BF16X6, t.BF16X3):
+        ws = torch.empty(t.tri_edm_workspace_size(n, d, prec), dtype=torch.uint8, device=D)
+        ref = torch.empty(size, device=D)
+        nf_ref = torch.zeros(1, dtype=torch.int64, device=D)
+        t.tri_edm(torch.from_numpy(x).to(D), ref, prec=prec, workspace=ws, n_flagged=nf_ref)
+        xh = torch.from_numpy(x).pin_memory()
+        oh = torch.full((size,), -1.0).pin_memory()
+        xd = torch.empty(n, d, device=D)
+        od = torch.empty(size, device=D)
+        nf = torch.zeros(1, dtype=torch.int64, device=D)
+        t.tri_edm_host(xh, oh, xd, od, ws, prec=prec, bands=bands, n_flagged=nf)
+        torch.cuda.synchronize()
+        assert int(ws[8:12].view(torch.int32).item()) == 0
+        assert torch.equal(oh, ref.cpu()), (prec, bands)
+        assert torch.equal(od, ref)
+        assert int(nf.item()) == int(nf_ref.item()) > 0
+
+
+def test_tc_edm_host_list_overflow_per_band(orc):
+    # every pair flagged (identical points): each band falls back to scanning its own rows
+    import torch
+    t = tri()
+    D = dev()
+    x = np.repeat(inputs.edm_normal_points(1, 40, seed=3), 1500, axis=0)
+    x[::97] += 0.5
+    n, d = x.shape
+    size = n * (n + 1) // 2
+    ws = torch.empty(t.tri_edm_workspace_size(n, d, t.BF16X6), dtype=torch.uint8, device=D)
+    xh = torch.from_numpy(x).pin_memory()
+    oh = torch.zeros(size).pin_memory()
+    nf = torch.zeros(1, dtype=torch.int64, device=D)
+    t.tri_edm_host(xh, oh, torch.empty(n, d, device=D), torch.empty(size, device=D), ws, prec=t.BF16X6, bands=4,
+                   n_flagged=nf)
+    torch.cuda.synchronize()
+    assert int(nf.item()) > 1 << 20
+    assert rel_err(oh.numpy(), orc.edm_packed(x)) <= 1e-5
+
+
+def test_tc_edm_host_errors():
+    import torch
+    t = tri()
+    D = dev()
+    xh = torch.zeros(10, 4).pin_memory()
+    ws = torch.empty(t.tri_edm_workspace_size(10, 4, t.BF16X6), dtype=torch.uint8, device=D)
+    with pytest.raises(t.TriError) as e:  # FP32 has no host-buffer path
+        t.tri_edm_host(xh, torch.zeros(55).pin_memory(), torch.empty(10, 4, device=D), torch.empty(55, device=D), ws,
+                       prec=t.FP32)
+    assert e.value.status == t.TRI_EINVAL
+    with pytest.raises(ValueError):  # host buffers must be host tensors
+        t.tri_edm_host(xh.to(D), torch.zeros(55), torch.empty(10, 4, device=D), torch.empty(55, device=D), ws)
