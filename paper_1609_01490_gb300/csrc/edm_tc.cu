@@ -61,7 +61,7 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up af
 constexpr int TQ = 8;                      // tile queue slots (producer -> MMA and epilogue)
 constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last tile
 constexpr uint32_t STATIC_PCT = 80;        // share of the tiles assigned up front, in contiguous runs
-constexpr uint32_t DYN_CHUNK = 8;          // tiles per grab from the global counter afterwards
+constexpr uint32_t DYN_CHUNK = 2;          // units per grab from the global counter afterwards
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int MAX_STAGES = 12;             // B ring depth cap (16 KB stages)
 
