@@ -989,10 +989,12 @@ cudaError_t launch_gram(const CUtensorMap &tmap, GramArgs g, size_t smem, cudaSt
 {
     cudaError_t e = cudaFuncSetAttribute(gram_kernel<MP, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    static std::mutex mu;
     static int cached_dev = -1, cached_pairs = 0;
     static size_t cached_smem = 0;
     int dev = 0;
     cudaGetDevice(&dev);
+    std::unique_lock<std::mutex> lock(mu);
     if (cached_dev != dev || cached_smem != smem) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (num_sms() / 2));
@@ -1008,8 +1010,10 @@ cudaError_t launch_gram(const CUtensorMap &tmap, GramArgs g, size_t smem, cudaSt
         cached_smem = smem;
         cached_pairs = ncl;
     }
+    const int npairs = cached_pairs;
+    lock.unlock();
     const uint64_t units = g.nunits - g.u0;
-    const uint64_t pairs = std::min<uint64_t>((uint64_t)(cached_pairs > 0 ? cached_pairs : 1), units);
+    const uint64_t pairs = std::min<uint64_t>((uint64_t)(npairs > 0 ? npairs : 1), units);
     g.static_per = units * STATIC_PCT / 100 / pairs;
     g.dyn_start = g.u0 + g.static_per * pairs;
     g.chunk = DYN_CHUNK;
