@@ -14,7 +14,11 @@ namespace {
 // the four consecutive tile rows 4ty .. 4ty+3.  The halo tile holds S+2 rows
 // of RHO+2 words (one word either side), cell bytes normalised to 0/1 and
 // zeroed outside the domain.
-template <int MAP, int RHO>
+// LIFE: the rule is Conway's (birth on 3, survival on 2 or 3), evaluated with
+// two SIMD byte compares on the 3 x 3 sum including the cell itself (alive
+// next iff the sum is 3, or 4 with the cell alive); otherwise the general
+// outer-totalistic rule is looked up per byte in `table`.
+template <int MAP, int RHO, bool LIFE>
 __global__ void __launch_bounds__(RHO *RHO) ca_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
                                                       uint32_t n, size_t ld, uint32_t table, BlockMap bm)
 {
@@ -56,11 +60,15 @@ __global__ void __launch_bounds__(RHO *RHO) ca_kernel(const uint8_t *__restrict_
         const long long wc = wc0 + 1 + tx;
         if (4 * wc > a) continue;
         const uint32_t alive = ctr[q + 1];
-        const uint32_t cnt = hs[q] + hs[q + 1] + hs[q + 2] - alive;  // 0..8 per byte
-        const uint32_t idx = cnt + (alive << 3) + alive;             // count + 9*alive
+        const uint32_t sum = hs[q] + hs[q + 1] + hs[q + 2];  // 3 x 3 sum, 0..9 per byte
         uint32_t nxt = 0;
+        if constexpr (LIFE) {
+            nxt = (__vcmpeq4(sum, 0x03030303u) | (__vcmpeq4(sum, 0x04040404u) & (alive * 0xFFu))) & 0x01010101u;
+        } else {
+            const uint32_t idx = sum + (alive << 3);  // count + 9*alive = sum - alive + 9*alive
 #pragma unroll
-        for (int b = 0; b < 4; ++b) nxt |= ((table >> ((idx >> (8 * b)) & 0xFFu)) & 1u) << (8 * b);
+            for (int b = 0; b < 4; ++b) nxt |= ((table >> ((idx >> (8 * b)) & 0xFFu)) & 1u) << (8 * b);
+        }
         uint8_t *dst = out + (size_t)a * ld + 4 * wc;
         if (4 * wc + 3 <= a) {
             *reinterpret_cast<uint32_t *>(dst) = nxt;
@@ -70,15 +78,26 @@ __global__ void __launch_bounds__(RHO *RHO) ca_kernel(const uint8_t *__restrict_
     }
 }
 
+template <int MAP, bool LIFE>
+void launch_rule(uint32_t rho, dim3 g, cudaStream_t s, const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
+                 uint32_t table, BlockMap bm)
+{
+    switch (rho) {
+    case 8: ca_kernel<MAP, 8, LIFE><<<g, dim3(8, 8), 0, s>>>(in, out, n, ld, table, bm); break;
+    case 16: ca_kernel<MAP, 16, LIFE><<<g, dim3(16, 16), 0, s>>>(in, out, n, ld, table, bm); break;
+    default: ca_kernel<MAP, 32, LIFE><<<g, dim3(32, 32), 0, s>>>(in, out, n, ld, table, bm); break;
+    }
+}
+
+// Conway's rule as a table: birth on 3 (bit 3), survival on 2 or 3 (bits 9 + 2, 9 + 3).
+constexpr uint32_t LIFE_TABLE = (1u << 3) | (1u << (9 + 2)) | (1u << (9 + 3));
+
 template <int MAP>
 cudaError_t launch_rho(uint32_t rho, dim3 g, cudaStream_t s, const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
                        uint32_t table, BlockMap bm)
 {
-    switch (rho) {
-    case 8: ca_kernel<MAP, 8><<<g, dim3(8, 8), 0, s>>>(in, out, n, ld, table, bm); break;
-    case 16: ca_kernel<MAP, 16><<<g, dim3(16, 16), 0, s>>>(in, out, n, ld, table, bm); break;
-    default: ca_kernel<MAP, 32><<<g, dim3(32, 32), 0, s>>>(in, out, n, ld, table, bm); break;
-    }
+    if (table == LIFE_TABLE) launch_rule<MAP, true>(rho, g, s, in, out, n, ld, table, bm);
+    else launch_rule<MAP, false>(rho, g, s, in, out, n, ld, table, bm);
     return cudaGetLastError();
 }
 
