@@ -384,7 +384,9 @@ def main():
 
     def step(map_id, pr=prec, record=False):
         if pr == tri.FP32:
-            tri.tri_edm(x, out, map=map_id, rho=16, reg=4, prec=pr)
+            # the FP32 comparison arm in its fastest measured shape: 8 x 8 pairs per
+            # thread at high d (compute-bound), 4 x 4 at low d (store-bound)
+            tri.tri_edm(x, out, map=map_id, rho=16, reg=8 if D_FEAT >= 32 else 4, prec=pr)
             return
         if not record:
             tri.tri_edm(x, out, map=map_id, prec=pr, workspace=ws, n_flagged=flagged)
@@ -452,7 +454,7 @@ def main():
         flops = 3.0 * D_FEAT * P  # sub, mul, add per feature and pair
         achieved = flops / (ms_step * 1e-3) / 1e12
         peak = NUM_SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "edm_kernel<lambda,16,4>", "achieved": achieved, "peak": peak,
+        roof = {"bound": "alu", "kernel": f"edm_kernel<lambda,16,{8 if D_FEAT >= 32 else 4}>", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz (derived)"}
         roof_alt = None
@@ -506,7 +508,8 @@ def main():
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "bf16x6": "bf16"}[args.prec],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP, "map": "lambda",
-                   "tile": ("16x16 threads x 4x4 pairs" if prec == tri.FP32
+                   "tile": (("16x16 threads x 8x8 pairs" if D_FEAT >= 32 else "16x16 threads x 4x4 pairs")
+                            if prec == tri.FP32
                             else "2x2 blocks of 128x128 tiles per CTA pair (tcgen05.mma.cta_group::2, M=N=256)"),
                    "prec": args.prec, "pairs_per_step": P,
                    "l2": (f"each step writes the {4 * P / 1e9:.2f} GB triangle (> 129 MB L2), which flushes L2 "

@@ -136,10 +136,13 @@ TRI_API int tri_lambda_verify(int sqrt_kind, int with_diag, uint64_t w_begin, ui
  *   out[i(i+1)/2 + j] = sqrt(sum_k (x[i][k] - x[j][k])^2), the diagonal 0.
  *   x (device, FP32) row-major [n][d]; out (device, FP32) n(n+1)/2 entries.
  *   prec = TRI_FP32: blocks of rho x rho threads, each thread reg x reg pairs
- *   (reg in {1, 2, 4}; 0 picks 4); each block covers an
- *   S x S pair tile, S = rho*reg, placed by `map` (any tri_map).  No workspace.
- *   prec = TRI_BF16X3 / TRI_BF16X6: 128 x 128 pair tiles on tcgen05 tensor
- *   cores, placed by TRI_MAP_LAMBDA or TRI_MAP_BB; rho and reg are ignored;
+ *   (reg in {1, 2, 4, 8}, 8 only with rho <= 16; 0 picks 4); each block covers
+ *   an S x S pair tile, S = rho*reg, placed by `map` (any tri_map).  For reg
+ *   >= 2 a thread updates two adjacent columns per f32x2 instruction.  No
+ *   workspace.
+ *   prec = TRI_BF16X3 / TRI_BF16X6: 2 x 2 blocks of 128 x 128 pair tiles per
+ *   CTA pair on tcgen05 tensor cores (cta_group::2), placed by
+ *   TRI_MAP_LAMBDA or TRI_MAP_BB; rho and reg are ignored;
  *   needs `workspace` of tri_edm_workspace_size bytes (256-byte aligned).
  *   Pairs whose Gram estimate of d^2 falls below tau*(|x_i|^2 + |x_j|^2) are
  *   recomputed in FP64 by direct differences; n_flagged (device uint64,
@@ -218,7 +221,7 @@ TRI_API int tri_edm_host(const float *x_host, uint32_t n, uint32_t d, float *out
  *   n_k (device uint32 [count]): points in instance k (0 allowed);
  *   out_cat (device FP32) / out_off (device uint64 [count]): instance k's
  *   packed triangle starts at out_cat + out_off[k].
- *   rho in {8,16,32}, reg in {1,2,4} as in tri_edm (FP32 direct differences).
+ *   rho in {8,16,32}, reg in {1,2,4,8} as in tri_edm (FP32 direct differences).
  *   workspace: tri_edm_batched_workspace_size bytes.  Issues two kernels and
  *   no host synchronisation, so it can be captured in a CUDA graph.
  *   Errors: TRI_EINVAL, TRI_ENOSPACE, TRI_ECUDA; an instance whose block count

@@ -16,19 +16,57 @@ constexpr int KC = 32;  // features staged per shared-memory pass
 // d features): rows i0 = bi*S.., columns j0 = bj*S...  Thread (ty, tx) owns
 // rows ty + u*RHO and columns tx + v*RHO (u, v < R), so a warp's stores for
 // fixed (u, v) fall on consecutive columns of one or two rows.
+// Two FP32 lanes per instruction (IEEE round-to-nearest in each lane): the
+// same results as two scalar subtractions and fused multiply-adds.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Row pitch of the staged column points: even, so that a thread's two
+// adjacent columns load as one 8-byte word.
+template <int RHO, int R>
+__host__ __device__ constexpr int sj_pitch() { return RHO * R + 2; }
+
+// One (RHO R) x (RHO R) tile.  Thread (ty, tx) owns rows ty + u RHO and, for
+// R = 1, column tx; for R >= 2, the column pairs 2 tx + 2 RHO v + {0, 1}
+// (v < R / 2), updated two at a time with f32x2 instructions, so that a
+// warp's 16 threads of a row cover 32 consecutive columns.
 template <int RHO, int R>
 __device__ __forceinline__ void edm_tile(const float *__restrict__ x, uint32_t n, uint32_t d,
                                          float *__restrict__ out, uint32_t bi, uint32_t bj,
-                                         float (*si)[RHO * R + 1], float (*sj)[RHO * R + 1])
+                                         float (*si)[RHO * R + 1], float (*sj)[sj_pitch<RHO, R>()])
 {
     constexpr int S = RHO * R;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RHO + tx;
     const uint64_t i0 = (uint64_t)bi * S, j0 = (uint64_t)bj * S;
-    float acc[R][R];
+    constexpr int RC = R == 1 ? 1 : R / 2;  // column groups per thread
+    // acc2[u][v]: packed partial sums of row u with columns c(v) and c(v) + 1 (R >= 2);
+    // for R = 1 the low half holds the single pair
+    unsigned long long acc2[R][RC];
 #pragma unroll
     for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int v = 0; v < R; ++v) acc[u][v] = 0.0f;
+        for (int v = 0; v < RC; ++v) acc2[u][v] = 0ull;
 
     for (uint32_t k0 = 0; k0 < d; k0 += KC) {
         const uint32_t kc = min((uint32_t)KC, d - k0);
@@ -40,20 +78,32 @@ __device__ __forceinline__ void edm_tile(const float *__restrict__ x, uint32_t n
             sj[k][r] = gj < n ? x[gj * d + k0 + k] : 0.0f;
         }
         __syncthreads();
+        if constexpr (R == 1) {
+            float acc = __uint_as_float((uint32_t)acc2[0][0]);
 #pragma unroll 4
-        for (uint32_t k = 0; k < kc; ++k) {
-            float a[R], b[R];
+            for (uint32_t k = 0; k < kc; ++k) {
+                const float df = si[k][ty] - sj[k][tx];
+                acc = fmaf(df, df, acc);
+            }
+            acc2[0][0] = __float_as_uint(acc);
+        } else {
+#pragma unroll 4
+            for (uint32_t k = 0; k < kc; ++k) {
+                unsigned long long b2[RC];
 #pragma unroll
-            for (int u = 0; u < R; ++u) a[u] = si[k][ty + u * RHO];
+                for (int v = 0; v < RC; ++v)
+                    b2[v] = *reinterpret_cast<const unsigned long long *>(&sj[k][2 * tx + 2 * RHO * v]);
 #pragma unroll
-            for (int v = 0; v < R; ++v) b[v] = sj[k][tx + v * RHO];
+                for (int u = 0; u < R; ++u) {
+                    const float a = si[k][ty + u * RHO];
+                    const unsigned long long a2 = f2_pack(a, a);
 #pragma unroll
-            for (int u = 0; u < R; ++u)
-#pragma unroll
-                for (int v = 0; v < R; ++v) {
-                    const float df = a[u] - b[v];
-                    acc[u][v] = fmaf(df, df, acc[u][v]);
+                    for (int v = 0; v < RC; ++v) {
+                        const unsigned long long df = f2_sub(a2, b2[v]);
+                        acc2[u][v] = f2_fma(df, df, acc2[u][v]);
+                    }
                 }
+            }
         }
         __syncthreads();
     }
@@ -62,10 +112,18 @@ __device__ __forceinline__ void edm_tile(const float *__restrict__ x, uint32_t n
         const uint64_t i = i0 + ty + u * RHO;
         if (i >= n) continue;
         float *row = out + T2(i);
+        if constexpr (R == 1) {
+            const uint64_t j = j0 + tx;
+            if (j <= i) row[j] = sqrtf(__uint_as_float((uint32_t)acc2[0][0]));
+        } else {
 #pragma unroll
-        for (int v = 0; v < R; ++v) {
-            const uint64_t j = j0 + tx + v * RHO;
-            if (j <= i) row[j] = sqrtf(acc[u][v]);
+            for (int v = 0; v < RC; ++v) {
+                const uint64_t j = j0 + 2 * tx + 2 * RHO * v;
+                float lo, hi;
+                f2_unpack(acc2[u][v], lo, hi);
+                if (j <= i) row[j] = sqrtf(lo);
+                if (j + 1 <= i) row[j + 1] = sqrtf(hi);
+            }
         }
     }
 }
@@ -75,7 +133,7 @@ __global__ void __launch_bounds__(RHO *RHO) edm_kernel(const float *__restrict__
                                                        float *__restrict__ out, BlockMap bm)
 {
     __shared__ float si[KC][RHO * R + 1];
-    __shared__ float sj[KC][RHO * R + 1];
+    __shared__ __align__(8) float sj[KC][sj_pitch<RHO, R>()];
     uint32_t bi, bj;
     if (!map_block<MAP>(bm, bi, bj)) return;
     edm_tile<RHO, R>(x, n, d, out, bi, bj, si, sj);
@@ -114,8 +172,8 @@ cudaError_t launch_rr(uint32_t rho, uint32_t reg, dim3 g, cudaStream_t s, const 
 {
 #define TRI_E(RH, RG)                                                                                          \
     if (rho == RH && reg == RG) return launch_one<MAP, RH, RG>(g, s, x, n, d, out, bm);
-    TRI_E(8, 1) TRI_E(8, 2) TRI_E(8, 4) TRI_E(16, 1) TRI_E(16, 2) TRI_E(16, 4) TRI_E(32, 1) TRI_E(32, 2)
-    TRI_E(32, 4)
+    TRI_E(8, 1) TRI_E(8, 2) TRI_E(8, 4) TRI_E(8, 8) TRI_E(16, 1) TRI_E(16, 2) TRI_E(16, 4) TRI_E(16, 8)
+    TRI_E(32, 1) TRI_E(32, 2) TRI_E(32, 4)
 #undef TRI_E
     return cudaErrorInvalidValue;
 }
@@ -171,7 +229,7 @@ __global__ void __launch_bounds__(RHO *RHO)
                        const uint64_t *__restrict__ out_off, const uint64_t *__restrict__ boff, uint32_t smem_cnt)
 {
     __shared__ float si[KC][RHO * R + 1];
-    __shared__ float sj[KC][RHO * R + 1];
+    __shared__ __align__(8) float sj[KC][sj_pitch<RHO, R>()];
     extern __shared__ uint64_t soff[];
     const bool in_smem = smem_cnt >= count + 1;
     if (in_smem)
@@ -220,7 +278,8 @@ int trihost::edm_fp32(const float *x, uint32_t n, uint32_t d, float *out, int ma
                       cudaStream_t s)
 {
     if (reg == 0) reg = 4;  // 4 x 4 pairs per thread: fastest at every d measured (3, 64, 128)
-    if (reg != 1 && reg != 2 && reg != 4) return TRI_EINVAL;
+    // 8 x 8 pairs per thread only with rho <= 16 (registers and static shared memory)
+    if ((reg != 1 && reg != 2 && reg != 4 && reg != 8) || (reg == 8 && rho > 16)) return TRI_EINVAL;
     if (map == TRI_MAP_UTM) {
         const uint64_t N = (uint64_t)n + 1, total = N * n / 2, tpb = (uint64_t)rho * rho;
         if (total > 0xFFFFFFFFull) return TRI_ERANGE;
@@ -287,7 +346,8 @@ extern "C" int tri_edm_batched(const float *x_cat, const uint64_t *pt_off, const
         return TRI_EINVAL;
     if (!trihost::rho_ok(rho)) return TRI_EINVAL;
     if (reg == 0) reg = 4;  // 4 x 4 pairs per thread: fastest at every d measured (3, 64, 128)
-    if (reg != 1 && reg != 2 && reg != 4) return TRI_EINVAL;
+    // 8 x 8 pairs per thread only with rho <= 16 (registers and static shared memory)
+    if ((reg != 1 && reg != 2 && reg != 4 && reg != 8) || (reg == 8 && rho > 16)) return TRI_EINVAL;
     size_t need = 0;
     tri_edm_batched_workspace_size(count, &need);
     if (ws_bytes < need || ((uintptr_t)workspace & 15)) return TRI_ENOSPACE;
@@ -301,8 +361,8 @@ extern "C" int tri_edm_batched(const float *x_cat, const uint64_t *pt_off, const
 #define TRI_B(RH, RG)                                                                                          \
     if (rho == RH && reg == RG)                                                                                \
         e = launch_batched_one<RH, RG>(s, x_cat, pt_off, n_k, count, d, out_cat, out_off, boff);
-    TRI_B(8, 1) TRI_B(8, 2) TRI_B(8, 4) TRI_B(16, 1) TRI_B(16, 2) TRI_B(16, 4) TRI_B(32, 1) TRI_B(32, 2)
-    TRI_B(32, 4)
+    TRI_B(8, 1) TRI_B(8, 2) TRI_B(8, 4) TRI_B(8, 8) TRI_B(16, 1) TRI_B(16, 2) TRI_B(16, 4) TRI_B(16, 8)
+    TRI_B(32, 1) TRI_B(32, 2) TRI_B(32, 4)
 #undef TRI_B
     return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }

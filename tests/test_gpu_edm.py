@@ -29,7 +29,7 @@ def _edm(t, x, map_id, rho, reg, guard=64):
 
 
 @pytest.mark.parametrize("mapname", ["LAMBDA", "LAMBDA_PDELTA", "BB", "RB", "REC", "UTM"])
-@pytest.mark.parametrize("rho,reg", [(8, 1), (16, 1), (32, 1), (8, 4), (16, 2), (16, 4), (32, 4)])
+@pytest.mark.parametrize("rho,reg", [(8, 1), (16, 1), (32, 1), (8, 4), (16, 2), (16, 4), (32, 4), (8, 8), (16, 8)])
 def test_edm_fp32_all_maps(orc, mapname, rho, reg):
     t = tri()
     map_id = getattr(t, "MAP_" + mapname)
@@ -87,5 +87,7 @@ def test_edm_rejects_bad_arguments():
         t.tri_edm(x, out, rho=12)
     with pytest.raises(t.TriError):
         t.tri_edm(x, out, reg=3)
+    with pytest.raises(t.TriError):  # 8 x 8 pairs per thread needs rho <= 16
+        t.tri_edm(x, out, rho=32, reg=8)
     with pytest.raises(t.TriError):  # REC needs a power-of-two block count: 40 points / 8 = 5
         t.tri_edm(torch.zeros(40, 3, device=dev()), torch.zeros(820, device=dev()), map=t.MAP_REC, rho=8, reg=1)
