@@ -51,11 +51,14 @@ __host__ __device__ constexpr int sj_pitch() { return RHO * R + 2; }
 // R = 1, column tx; for R >= 2, the column pairs 2 tx + 2 RHO v + {0, 1}
 // (v < R / 2), updated two at a time with f32x2 instructions, so that a
 // warp's 16 threads of a row cover 32 consecutive columns.
+// Not inlined: every block map calls the same compiled tile body, so the maps
+// differ only in how a block finds its (bi, bj).
 template <int RHO, int R>
-__device__ __forceinline__ void edm_tile(const float *__restrict__ x, uint32_t n, uint32_t d,
-                                         float *__restrict__ out, uint32_t bi, uint32_t bj,
-                                         float (*si)[RHO * R + 1], float (*sj)[sj_pitch<RHO, R>()])
+__device__ __noinline__ void edm_tile(const float *__restrict__ x, uint32_t n, uint32_t d,
+                                      float *__restrict__ out, uint32_t bi, uint32_t bj)
 {
+    __shared__ float si[KC][RHO * R + 1];
+    __shared__ __align__(8) float sj[KC][sj_pitch<RHO, R>()];
     constexpr int S = RHO * R;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RHO + tx;
     const uint64_t i0 = (uint64_t)bi * S, j0 = (uint64_t)bj * S;
@@ -132,11 +135,9 @@ template <int MAP, int RHO, int R>
 __global__ void __launch_bounds__(RHO *RHO) edm_kernel(const float *__restrict__ x, uint32_t n, uint32_t d,
                                                        float *__restrict__ out, BlockMap bm)
 {
-    __shared__ float si[KC][RHO * R + 1];
-    __shared__ __align__(8) float sj[KC][sj_pitch<RHO, R>()];
     uint32_t bi, bj;
     if (!map_block<MAP>(bm, bi, bj)) return;
-    edm_tile<RHO, R>(x, n, d, out, bi, bj, si, sj);
+    edm_tile<RHO, R>(x, n, d, out, bi, bj);
 }
 
 // UTM is a thread-space map: one thread per pair, no tile to stage.
@@ -228,8 +229,6 @@ __global__ void __launch_bounds__(RHO *RHO)
                        const uint32_t *__restrict__ n_k, uint32_t count, uint32_t d, float *__restrict__ out_cat,
                        const uint64_t *__restrict__ out_off, const uint64_t *__restrict__ boff, uint32_t smem_cnt)
 {
-    __shared__ float si[KC][RHO * R + 1];
-    __shared__ __align__(8) float sj[KC][sj_pitch<RHO, R>()];
     extern __shared__ uint64_t soff[];
     const bool in_smem = smem_cnt >= count + 1;
     if (in_smem)
@@ -247,7 +246,7 @@ __global__ void __launch_bounds__(RHO *RHO)
         }
         uint32_t bi, bj;
         lambda_diag<TRI_SQRT_R>((uint32_t)(wg - off[lo]), bi, bj);
-        edm_tile<RHO, R>(x_cat + pt_off[lo] * d, n_k[lo], d, out_cat + out_off[lo], bi, bj, si, sj);
+        edm_tile<RHO, R>(x_cat + pt_off[lo] * d, n_k[lo], d, out_cat + out_off[lo], bi, bj);
     }
 }
 
