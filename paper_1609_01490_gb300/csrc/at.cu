@@ -9,12 +9,43 @@ using namespace tri;
 
 namespace {
 
+// Two FP32 lanes per instruction (IEEE round-to-nearest in each lane).
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+#define TRI_F2_OP(NAME, OP)                                                                                   \
+    __device__ __forceinline__ f2 NAME(f2 a, f2 b)                                                           \
+    {                                                                                                        \
+        f2 r;                                                                                                \
+        asm(OP ".rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));                                          \
+        return r;                                                                                            \
+    }
+TRI_F2_OP(f2_add, "add")
+TRI_F2_OP(f2_sub, "sub")
+TRI_F2_OP(f2_mul, "mul")
+#undef TRI_F2_OP
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Block (L, R, C), L >= R >= C, of rho x rho threads: thread (ty, tx) takes
 // i = L*rho + ty and j = R*rho + tx and loops k over block C (k < j).  With
 // squared sides a = |ij|^2, b = |jk|^2, c = |ki|^2 the law of cosines gives
 // cos g_i cos g_j cos g_k = (a+c-b)(a+b-c)(b+c-a) / (8abc) and
 // (r_ij r_jk r_ki)^3 = (abc)^(3/2).  Terms are formed and summed per thread in
-// FP32, then reduced over the block in FP64 into partial[T3(L)+T2(R)+C].
+// FP32 (two k at a time with f32x2 instructions, into two running sums), summed
+// over each warp in FP32 and over the warps in FP64 into partial[T3(L)+T2(R)+C].
 template <int MAP>
 __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, uint32_t m, uint64_t nblocks,
                           double *__restrict__ partial)
@@ -30,15 +61,16 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
         L = blockIdx.z;
         if (R > L || C > R) return;
     }
-    __shared__ float pk[32][3];
+    // block C's points by coordinate, so that two consecutive k load as one 8-byte word
+    __shared__ __align__(8) float pkx[32], pky[32], pkz[32];
     __shared__ double wsum[32];
     const uint32_t rho = blockDim.x;
     const uint32_t tid = threadIdx.y * rho + threadIdx.x;
     if (tid < rho) {
         const uint32_t k = C * rho + tid;
-        pk[tid][0] = k < n ? p[3 * k + 0] : 0.0f;
-        pk[tid][1] = k < n ? p[3 * k + 1] : 0.0f;
-        pk[tid][2] = k < n ? p[3 * k + 2] : 0.0f;
+        pkx[tid] = k < n ? p[3 * k + 0] : 0.0f;
+        pky[tid] = k < n ? p[3 * k + 1] : 0.0f;
+        pkz[tid] = k < n ? p[3 * k + 2] : 0.0f;
     }
     __syncthreads();
     const uint32_t i = L * rho + threadIdx.y, j = R * rho + threadIdx.x;
@@ -49,9 +81,32 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
         const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
         const float a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const uint32_t kend = min(j, (C + 1) * rho) - C * rho;  // k < j
-        for (uint32_t t = 0; t < kend; ++t) {
-            const float ex = xj - pk[t][0], ey = yj - pk[t][1], ez = zj - pk[t][2];
-            const float fx = pk[t][0] - xi, fy = pk[t][1] - yi, fz = pk[t][2] - zi;
+        const f2 XJ = f2_pack(xj, xj), YJ = f2_pack(yj, yj), ZJ = f2_pack(zj, zj);
+        const f2 XI = f2_pack(xi, xi), YI = f2_pack(yi, yi), ZI = f2_pack(zi, zi);
+        const f2 A = f2_pack(a, a), K = f2_pack(0.375f, 0.375f), ONE = f2_pack(1.0f, 1.0f);
+        f2 S = f2_pack(0.0f, 0.0f);
+        uint32_t t = 0;
+        for (; t + 1 < kend; t += 2) {
+            const f2 PX = *reinterpret_cast<const f2 *>(&pkx[t]), PY = *reinterpret_cast<const f2 *>(&pky[t]),
+                     PZ = *reinterpret_cast<const f2 *>(&pkz[t]);
+            const f2 ex = f2_sub(XJ, PX), ey = f2_sub(YJ, PY), ez = f2_sub(ZJ, PZ);
+            const f2 fx = f2_sub(PX, XI), fy = f2_sub(PY, YI), fz = f2_sub(PZ, ZI);
+            const f2 b = f2_fma(ex, ex, f2_fma(ey, ey, f2_mul(ez, ez)));
+            const f2 c = f2_fma(fx, fx, f2_fma(fy, fy, f2_mul(fz, fz)));
+            const f2 q = f2_mul(f2_mul(A, b), c);
+            const f2 P = f2_mul(f2_mul(f2_sub(f2_add(A, c), b), f2_sub(f2_add(A, b), c)), f2_sub(f2_add(b, c), A));
+            float q0, q1;
+            f2_unpack(q, q0, q1);
+            const f2 rs = f2_pack(rsqrtf(q0), rsqrtf(q1));
+            const f2 inv = f2_mul(rs, rs);
+            S = f2_add(S, f2_mul(f2_mul(f2_fma(f2_mul(K, P), inv, ONE), inv), rs));
+        }
+        float s0, s1;
+        f2_unpack(S, s0, s1);
+        s = s0 + s1;
+        for (; t < kend; ++t) {
+            const float ex = xj - pkx[t], ey = yj - pky[t], ez = zj - pkz[t];
+            const float fx = pkx[t] - xi, fy = pky[t] - yi, fz = pkz[t] - zi;
             const float b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
             const float c = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
             const float q = a * b * c;
@@ -61,15 +116,17 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
             s += fmaf(0.375f * P, inv, 1.0f) * inv * rs;
         }
     }
-    double v = nu * (double)s;
+    // warp sums in FP32 (5 more roundings of at most 2^-24 of the magnitude
+    // sum each; FP64 arithmetic is scarce on this part), warp totals in FP64
+    float v = s;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const uint32_t nthreads = rho * rho, lane = tid & 31, warp = tid >> 5;
-    if (lane == 0) wsum[warp] = v;
+    if (lane == 0) wsum[warp] = (double)v;
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
         for (uint32_t q = 0; q < (nthreads + 31) / 32; ++q) t += wsum[q];
-        partial[T3(L) + T2(R) + C] = t;
+        partial[T3(L) + T2(R) + C] = nu * t;
     }
 }
 
