@@ -238,14 +238,15 @@ TRI_API int tri_edm_batched_workspace_size(uint32_t count, size_t *bytes);
  * automaton (Game of Life: birth_mask = 1<<3, survive_mask = 1<<2 | 1<<3) on
  * the triangular domain {0 <= j <= i < n} (Section 1 lists cellular automata
  * on triangular domains among the TD problems; Section 5 motivates the
- * shared-memory tiled form).  A cell is alive when its byte is non-zero;
- * neighbours outside the domain count as dead.  Each block stages a halo
- * tile in shared memory; only domain cells of `out` are written (0 or 1).
- *   in, out (device uint8) row-major with leading dimension ld (bytes);
- *   ld >= n and ld a multiple of 16; in != out (no aliasing).
- *   map: LAMBDA, LAMBDA_PDELTA, BB, RB or REC.  rho in {8,16,32}: a block of
- *   rho x rho threads covers a (4 rho) x (4 rho) cell tile, each thread four
- *   4-cell words.
+ * tiled form).  A cell is alive when its byte is non-zero; neighbours
+ * outside the domain count as dead.  Each thread streams its strip's rows
+ * through registers (neighbouring strips exchange edge cells by warp
+ * shuffle); only domain cells of `out` are written (0 or 1).
+ *   in, out (device uint8, 16-byte aligned) row-major with leading dimension
+ *   ld (bytes); ld >= n and ld a multiple of 16; in != out (no aliasing).
+ *   map: LAMBDA, LAMBDA_PDELTA, BB, RB or REC.  rho in {8,16,32}: each block
+ *   covers a (4 rho) x (4 rho) cell tile with 4 rho threads, each thread a
+ *   16-cell strip of rho/4 consecutive rows (one 16-byte load per row).
  *   Errors: TRI_EINVAL (null, aliasing, bad ld/rho/map), TRI_ERANGE, TRI_ECUDA.
  */
 TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,

@@ -10,70 +10,94 @@ using namespace tri;
 
 namespace {
 
-// Tile: S x S cells, S = 4*RHO.  Thread (ty, tx) owns the 4-cell word tx of
-// the four consecutive tile rows 4ty .. 4ty+3.  The halo tile holds S+2 rows
-// of RHO+2 words (one word either side), cell bytes normalised to 0/1 and
-// zeroed outside the domain.
+// Tile: S x S cells, S = 4*RHO, in S/16 strips of 16 cells.  The block has S
+// threads: thread t takes strip c = t % NS (NS = S/16 strips) of the tile rows
+// [Hr g, Hr g + Hr), g = t / NS, Hr = S/16, and keeps its Hr + 2 input rows (one
+// above, one below) in registers as four 4-cell words each, loaded with one
+// 16-byte load per row.  The cell left (right) of the strip comes from the
+// neighbouring lane by shuffle, or, for the tile's first (last) strip, from a
+// 4-byte load beyond the tile.  Cell bytes are normalised to 0/1 and zeroed
+// outside the domain (j > i, rows outside [0, n)); the neighbour counts are
+// byte-SIMD sums.
 // LIFE: the rule is Conway's (birth on 3, survival on 2 or 3), evaluated with
 // two SIMD byte compares on the 3 x 3 sum including the cell itself (alive
 // next iff the sum is 3, or 4 with the cell alive); otherwise the general
 // outer-totalistic rule is looked up per byte in `table`.
 template <int MAP, int RHO, bool LIFE>
-__global__ void __launch_bounds__(RHO *RHO) ca_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
-                                                      uint32_t n, size_t ld, uint32_t table, BlockMap bm)
+__global__ void __launch_bounds__(4 * RHO) ca_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
+                                                     uint32_t n, size_t ld, uint32_t table, BlockMap bm)
 {
-    constexpr int S = 4 * RHO, W = RHO + 2, H = S + 2;
-    __shared__ uint32_t halo[H][W];
+    constexpr int S = 4 * RHO, NS = S / 16, HR = S / 16;
     uint32_t bi, bj;
     if (!map_block<MAP>(bm, bi, bj)) return;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RHO + tx;
-    const long long row0 = (long long)bi * S - 1;    // global row of halo row 0
-    const long long wc0 = (long long)bj * RHO - 1;   // global word column of halo word 0
-
-    for (int t = tid; t < H * W; t += RHO * RHO) {
-        const int y = t / W, w = t - y * W;
-        const long long a = row0 + y, wc = wc0 + w;
-        uint32_t v = 0;
-        if (a >= 0 && a < (long long)n && wc >= 0 && 4 * wc <= a) {
-            v = *reinterpret_cast<const uint32_t *>(in + (size_t)a * ld + 4 * wc);
-            v = __vcmpne4(v, 0u) & 0x01010101u;            // alive -> 1
-            const long long over = 4 * wc + 3 - a;         // bytes past the diagonal
-            if (over > 0) v &= 0xFFFFFFFFu >> (8 * over);  // cells j > a are outside
-        }
-        halo[y][w] = v;
-    }
-    __syncthreads();
-
-    // horizontal 3-sums of halo rows 4ty .. 4ty+5
-    uint32_t hs[6], ctr[6];
+    const int t = threadIdx.x, c = t % NS, g = t / NS;
+    const long long cc = (long long)bj * S + 16 * c;         // first cell (byte) column of the strip
+    const long long a0 = (long long)bi * S + HR * g - 1;     // global row of the first register row
+    // keep the domain part of the word at byte column col of row a (col a multiple of 4)
+    auto clip = [](uint32_t w, long long col, long long a) {
+        w = __vcmpne4(w, 0u) & 0x01010101u;  // alive -> 1
+        const long long over = col + 3 - a;  // bytes past the diagonal
+        return over <= 0 ? w : (over >= 4 ? 0u : w & (0xFFFFFFFFu >> (8 * over)));
+    };
+    uint32_t w[HR + 2][4], lw[HR + 2], rw[HR + 2];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const int y = 4 * ty + q;
-        const uint32_t L = halo[y][tx], C = halo[y][tx + 1], R = halo[y][tx + 2];
-        hs[q] = __funnelshift_l(L, C, 8) + C + __funnelshift_r(C, R, 8);
-        ctr[q] = C;
+    for (int q = 0; q < HR + 2; ++q) {
+        const long long a = a0 + q;
+        const bool rok = a >= 0 && a < (long long)n;
+        const uint8_t *row = in + (rok ? (size_t)a * ld : 0);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (rok && cc <= a) v = __ldg(reinterpret_cast<const uint4 *>(row + cc));
+        lw[q] = (c == 0 && rok && cc >= 4 && cc - 4 <= a) ? __ldg(reinterpret_cast<const uint32_t *>(row + cc - 4)) : 0u;
+        rw[q] = (c == NS - 1 && rok && cc + 16 <= a) ? __ldg(reinterpret_cast<const uint32_t *>(row + cc + 16)) : 0u;
+        w[q][0] = v.x;
+        w[q][1] = v.y;
+        w[q][2] = v.z;
+        w[q][3] = v.w;
+    }
+    // normalise, clip at the diagonal, fetch the neighbours' edge words, horizontal 3-sums
+    uint32_t hs[HR + 2][4], ctr[HR + 2][4];
+#pragma unroll
+    for (int q = 0; q < HR + 2; ++q) {
+        const long long a = a0 + q;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[q][k] = clip(w[q][k], cc + 4 * k, a);
+        const uint32_t lc = clip(lw[q], cc - 4, a), rc = clip(rw[q], cc + 16, a);
+        const uint32_t up = __shfl_up_sync(0xffffffffu, w[q][3], 1, NS);    // strip c - 1, last word
+        const uint32_t dn = __shfl_down_sync(0xffffffffu, w[q][0], 1, NS);  // strip c + 1, first word
+        const uint32_t L = c == 0 ? lc : up, R = c == NS - 1 ? rc : dn;
+        const uint32_t W0 = w[q][0], W1 = w[q][1], W2 = w[q][2], W3 = w[q][3];
+        hs[q][0] = __funnelshift_l(L, W0, 8) + W0 + __funnelshift_r(W0, W1, 8);
+        hs[q][1] = __funnelshift_l(W0, W1, 8) + W1 + __funnelshift_r(W1, W2, 8);
+        hs[q][2] = __funnelshift_l(W1, W2, 8) + W2 + __funnelshift_r(W2, W3, 8);
+        hs[q][3] = __funnelshift_l(W2, W3, 8) + W3 + __funnelshift_r(W3, R, 8);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ctr[q][k] = w[q][k];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const long long a = row0 + 1 + 4 * ty + q;
+    for (int q = 1; q <= HR; ++q) {
+        const long long a = a0 + q;
         if (a >= (long long)n) break;
-        const long long wc = wc0 + 1 + tx;
-        if (4 * wc > a) continue;
-        const uint32_t alive = ctr[q + 1];
-        const uint32_t sum = hs[q] + hs[q + 1] + hs[q + 2];  // 3 x 3 sum, 0..9 per byte
-        uint32_t nxt = 0;
-        if constexpr (LIFE) {
-            nxt = (__vcmpeq4(sum, 0x03030303u) | (__vcmpeq4(sum, 0x04040404u) & (alive * 0xFFu))) & 0x01010101u;
-        } else {
-            const uint32_t idx = sum + (alive << 3);  // count + 9*alive = sum - alive + 9*alive
+        if (cc > a) continue;  // the strip is past the diagonal in this row
+        uint32_t nxt[4];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) nxt |= ((table >> ((idx >> (8 * b)) & 0xFFu)) & 1u) << (8 * b);
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t alive = ctr[q][k];
+            const uint32_t sum = hs[q - 1][k] + hs[q][k] + hs[q + 1][k];  // 3 x 3 sum, 0..9 per byte
+            uint32_t r = 0;
+            if constexpr (LIFE) {
+                r = (__vcmpeq4(sum, 0x03030303u) | (__vcmpeq4(sum, 0x04040404u) & (alive * 0xFFu))) & 0x01010101u;
+            } else {
+                const uint32_t idx = sum + (alive << 3);  // count + 9*alive = sum - alive + 9*alive
+#pragma unroll
+                for (int b = 0; b < 4; ++b) r |= ((table >> ((idx >> (8 * b)) & 0xFFu)) & 1u) << (8 * b);
+            }
+            nxt[k] = r;
         }
-        uint8_t *dst = out + (size_t)a * ld + 4 * wc;
-        if (4 * wc + 3 <= a) {
-            *reinterpret_cast<uint32_t *>(dst) = nxt;
+        uint8_t *dst = out + (size_t)a * ld + cc;
+        if (cc + 15 <= a) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(nxt[0], nxt[1], nxt[2], nxt[3]);
         } else {
-            for (int b = 0; 4 * wc + b <= a; ++b) dst[b] = (uint8_t)(nxt >> (8 * b));
+            for (int b = 0; cc + b <= a; ++b) dst[b] = (uint8_t)(nxt[b >> 2] >> (8 * (b & 3)));
         }
     }
 }
@@ -83,9 +107,9 @@ void launch_rule(uint32_t rho, dim3 g, cudaStream_t s, const uint8_t *in, uint8_
                  uint32_t table, BlockMap bm)
 {
     switch (rho) {
-    case 8: ca_kernel<MAP, 8, LIFE><<<g, dim3(8, 8), 0, s>>>(in, out, n, ld, table, bm); break;
-    case 16: ca_kernel<MAP, 16, LIFE><<<g, dim3(16, 16), 0, s>>>(in, out, n, ld, table, bm); break;
-    default: ca_kernel<MAP, 32, LIFE><<<g, dim3(32, 32), 0, s>>>(in, out, n, ld, table, bm); break;
+    case 8: ca_kernel<MAP, 8, LIFE><<<g, 32, 0, s>>>(in, out, n, ld, table, bm); break;
+    case 16: ca_kernel<MAP, 16, LIFE><<<g, 64, 0, s>>>(in, out, n, ld, table, bm); break;
+    default: ca_kernel<MAP, 32, LIFE><<<g, 128, 0, s>>>(in, out, n, ld, table, bm); break;
     }
 }
 
@@ -107,7 +131,7 @@ extern "C" int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t l
                            uint32_t survive_mask, int map, uint32_t rho, void *stream)
 {
     if (!in || !out || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
-    if (ld < n || (ld & 15) || ((uintptr_t)in & 3) || ((uintptr_t)out & 3)) return TRI_EINVAL;
+    if (ld < n || (ld & 15) || ((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return TRI_EINVAL;
     // no aliasing: the two buffers of n rows must not overlap
     const size_t span = (size_t)(n - 1) * ld + n;
     if ((in < out + span) && (out < in + span)) return TRI_EINVAL;

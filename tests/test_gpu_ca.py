@@ -60,6 +60,17 @@ def test_ca_other_rule_and_patterns(orc):
         assert np.array_equal(got, orc.ca_run(g, 3, birth, survive))
 
 
+def test_ca_rejects_unaligned_buffers():
+    # rows are read and written 16 bytes at a time: both buffers must be 16-byte aligned
+    import torch
+    t = tri()
+    a = torch.zeros(64 * 48 + 16, dtype=torch.uint8, device=dev())
+    b = torch.zeros_like(a)
+    with pytest.raises(t.TriError) as e:
+        t.tri_ca_step(a[4:4 + 64 * 48].view(48, 64), b[:64 * 48].view(48, 64), 48)
+    assert e.value.status == t.TRI_EINVAL
+
+
 def test_ca_c1_size_one_step(orc):
     # the n = 16384 triangle (134,225,920 cells) of the Life workload: one step, every cell
     t = tri()
