@@ -137,6 +137,25 @@ def cpu_oracle_sample(x: np.ndarray, target_s: float = 12.0):
     return pairs / dt, oracle.threads(), f"rows [{r0}, {n}) of the triangle: {pairs} pairs in {dt:.2f} s"
 
 
+def max_over_ranks(values, world: int, device=None):
+    """Each timing's maximum over the ranks: in a replica run the slowest rank
+    bounds the job.  Collective over the default process group when world > 1."""
+    values = [float(v) for v in values]
+    if world <= 1:
+        return values
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(world: int, units_per_rank: float, ms_per_step: float) -> float:
+    """Whole-job throughput: the units every rank processed in one step over
+    the slowest rank's step time."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -424,11 +443,8 @@ def main():
     sampler.start()
     ms_lambda = timed(lambda: step(tri.MAP_LAMBDA, record=True), args.steps, 0)
     clocks = sampler.stop()
-    ms_t = torch.tensor([ms_lambda], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_step = float(ms_t.item())
-    value = world * P / (ms_step * 1e-3)
+    ms_step = max_over_ranks([ms_lambda], world, dev)[0]
+    value = job_rate(world, P, ms_step)
     n_flagged = int(flagged.item())
     phases = None
     if phase_events:
@@ -446,6 +462,7 @@ def main():
         ms_fp32 = ms_step
     else:
         ms_fp32 = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_LAMBDA, tri.FP32), 3, 1)
+    ms_bb, ms_fp32 = max_over_ranks([ms_bb, ms_fp32], world, dev)
 
     # ---- roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -496,8 +513,8 @@ def main():
             def e2e_step():
                 tri.tri_edm_host(xh, oh, x, out, ws, map=tri.MAP_LAMBDA, prec=prec, n_flagged=flagged)
 
-        ms_e2e = timed(e2e_step, max(2, min(args.steps, 5)), 1)
-        e2e = {"value": world * P / (ms_e2e * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": xh.numel() * 4,
+        ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), 1)], world, dev)[0]
+        e2e = {"value": job_rate(world, P, ms_e2e), "unit": "pairs/s", "h2d_bytes_per_step": xh.numel() * 4,
                "d2h_bytes_per_step": oh.numel() * 4,
                "path": "tri_edm_host" if prec != tri.FP32 else "copies around tri_edm"}
         del oh, xh
@@ -515,8 +532,8 @@ def main():
                    "l2": (f"each step writes the {4 * P / 1e9:.2f} GB triangle (> 129 MB L2), which flushes L2 "
                           "between steps" if 4 * P > 129e6 else
                           f"the {4 * P / 1e6:.1f} MB triangle fits in L2: no flush between steps")},
-        "bb": {"ms_per_step": ms_bb, "value": world * P / (ms_bb * 1e-3), "I_bb_over_lambda": ms_bb / ms_step},
-        "fp32_lambda": {"ms_per_step": ms_fp32, "value": world * P / (ms_fp32 * 1e-3),
+        "bb": {"ms_per_step": ms_bb, "value": job_rate(world, P, ms_bb), "I_bb_over_lambda": ms_bb / ms_step},
+        "fp32_lambda": {"ms_per_step": ms_fp32, "value": job_rate(world, P, ms_fp32),
                         "speedup_of_headline": ms_fp32 / ms_step},
         "clocks": clocks,
         "gpu_launches": args.steps * (1 if prec == tri.FP32 else 3),
