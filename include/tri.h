@@ -169,7 +169,7 @@ TRI_API int tri_edm_workspace_size(uint32_t n, uint32_t d, int prec, size_t *byt
  * stages); larger sizes give TRI_ERANGE.
  *
  *   tri_edm_prepare: clears the workspace header, then writes the FP32 row
- *     norms |x_i|^2 (summed in FP64) and the BF16 split planes (hi, lo or hi,
+ *     norms |x_i|^2 (summed to ~48 bits as FP32 pairs) and the BF16 split planes (hi, lo or hi,
  *     mid, lo; K zero-padded to a multiple of 64).
  *   tri_edm_gram: tensor-core Gram term, d^2 = |x_i|^2 + |x_j|^2 - 2 x_i.x_j,
  *     clamped at 0, square root stored to out (packed, FP32); pairs with

@@ -12,7 +12,7 @@
 // too many digits to cancellation and is flagged; a second kernel recomputes
 // flagged pairs in FP64 by direct differences (the paper's definition).
 //
-// Kernels.  prepare: FP64 row norms (stored as FP32) and the BF16 planes,
+// Kernels.  prepare: row norms (FP32 pairs, stored as FP32) and the BF16 planes,
 // K padded to a multiple of 64.  gram: persistent clusters of two CTAs on two
 // SMs (a CTA pair), one pair per two SMs.  A unit of work is a 2 x 2 block of
 // 128 x 128 pair tiles (row blocks 2R, 2R + 1, column blocks 2C, 2C + 1),
@@ -309,7 +309,19 @@ __device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
 }
 
 // ------------------------------------------------------------ prepare ----
-// One warp per row: FP64 norm (rounded to FP32) and the BF16 planes.
+// Error-free transformations on FP32 pairs (Knuth's TwoSum; the product error
+// from one FMA): a + b = s + e and a * a = p + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// One warp per row: the BF16 planes and the row norm |x|^2, summed as an
+// unevaluated pair hi + lo of FP32 numbers (products split exactly by FMA,
+// sums by TwoSum; about 48 significant bits, FP64 being scarce on this part),
+// rounded to FP32 once at the end.
 template <int P>
 __global__ void prepare_kernel(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t dp,
                                float *__restrict__ norms, __nv_bfloat16 *__restrict__ planes)
@@ -317,10 +329,14 @@ __global__ void prepare_kernel(const float *__restrict__ x, uint32_t n, uint32_t
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const float *row = x + (size_t)warp * d;
-    double s = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     for (uint32_t k = lane; k < dp; k += 32) {
         const float v = k < d ? row[k] : 0.0f;
-        s += (double)v * (double)v;
+        const float p = v * v, pe = fmaf(v, v, -p);  // v^2 = p + pe
+        float t, te;
+        two_sum(hi, p, t, te);
+        hi = t;
+        lo += te + pe;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const float r1 = v - __bfloat162float(hi);
         const size_t o = (size_t)warp * dp + k;
@@ -334,8 +350,14 @@ __global__ void prepare_kernel(const float *__restrict__ x, uint32_t n, uint32_t
             planes[2 * (size_t)n * dp + o] = __float2bfloat16_rn(r2);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) norms[warp] = (float)s;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o), ol = __shfl_down_sync(0xffffffffu, lo, o);
+        float t, te;
+        two_sum(hi, oh, t, te);
+        hi = t;
+        lo += ol + te;
+    }
+    if (lane == 0) norms[warp] = hi + lo;
 }
 
 // --------------------------------------------------------------- gram ----
@@ -907,19 +929,38 @@ __global__ void fixup_kernel(const float *__restrict__ x, uint32_t d, float *__r
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (uint64_t)gridDim.x * blockDim.x;
     if (tid == 0 && n_flagged) *n_flagged = cnt;
     if (tid == 0 && next_start) *next_start = cnt;
+    // by one thread: four independent partial sums, so the loads of
+    // consecutive features overlap
     auto recompute = [&](uint32_t i, uint32_t j) {
         const float *xi = x + (size_t)i * d, *xj = x + (size_t)j * d;
-        double s = 0.0;
-        for (uint32_t k = 0; k < d; ++k) {
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t k = 0;
+        for (; k + 4 <= d; k += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double df = (double)xi[k + u] - (double)xj[k + u];
+                s[u] = fma(df, df, s[u]);
+            }
+        for (; k < d; ++k) {
             const double df = (double)xi[k] - (double)xj[k];
-            s = fma(df, df, s);
+            s[0] = fma(df, df, s[0]);
         }
-        out[T2(i) + j] = (float)sqrt(s);
+        out[T2(i) + j] = (float)sqrt((s[0] + s[1]) + (s[2] + s[3]));
     };
     if (cnt <= cap) {
-        for (uint64_t e = first + tid; e < cnt; e += nth) {
+        // one warp per listed pair: lanes take strided features, then a fixed-order tree sum
+        const uint32_t lane = threadIdx.x & 31;
+        for (uint64_t e = first + (tid >> 5); e < cnt; e += nth >> 5) {
             const unsigned long long v = list[e];
-            recompute((uint32_t)(v >> 32), (uint32_t)(v & 0xFFFFFFFFu));
+            const uint32_t i = (uint32_t)(v >> 32), j = (uint32_t)(v & 0xFFFFFFFFu);
+            const float *xi = x + (size_t)i * d, *xj = x + (size_t)j * d;
+            double s = 0.0;
+            for (uint32_t k = lane; k < d; k += 32) {
+                const double df = (double)xi[k] - (double)xj[k];
+                s = fma(df, df, s);
+            }
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) out[T2(i) + j] = (float)sqrt(s);
         }
     } else {
         const float wide = 1.0625f * tau;
