@@ -8,7 +8,10 @@ Features of a (kernel, n, d, map, rho) candidate (14):
   kernel one-hot (edm, ca, at), map one-hot (lambda, lambda on P_Delta, BB,
   RB, REC, UTM), log2 of the tile side, standardised with the training set's
   mean and deviation.
-Target: log of the measured milliseconds.
+Target: log of the measured milliseconds relative to the configuration's
+default candidate (lambda, rho = 16): the sizes set a common scale that the
+ranking of maps does not depend on, so the model spends its capacity on the
+differences between candidates.
 """
 from __future__ import annotations
 
@@ -23,6 +26,7 @@ from . import tri
 from .autotune import KERNELS, MAPS, RHOS, applicable, cand_name
 
 MAP_ORDER = (tri.MAP_LAMBDA, tri.MAP_LAMBDA_PDELTA, tri.MAP_BB, tri.MAP_RB, tri.MAP_REC, tri.MAP_UTM)
+DEFAULT = (tri.MAP_LAMBDA, 16)  # the library's default candidate
 NFEAT = 14
 H1 = H2 = 64
 
@@ -72,15 +76,18 @@ def parse_name(name: str):
 
 
 def dataset(table: dict, groups):
-    """Rows (features, log ms) of the given groups of a sweep table."""
+    """Rows (features, log(ms / ms of the group's default candidate)) of the
+    given groups of a sweep table."""
     X, y = [], []
     for gkey in groups:
         kernel, n, d = gkey.split("|")
         n, d = int(n), int(d)
-        for name, ms in table["groups"][gkey].items():
+        tbl = table["groups"][gkey]
+        ref = tbl[cand_name(*DEFAULT)]
+        for name, ms in tbl.items():
             m, r = parse_name(name)
             X.append(features(kernel, n, d, m, r))
-            y.append(math.log(ms))
+            y.append(math.log(ms / ref))
     return np.array(X), np.array(y)
 
 
@@ -172,7 +179,7 @@ def train(X: np.ndarray, y: np.ndarray, steps: int = 3000, lr: float = 3e-3, see
     return model, float(loss.item())
 
 
-def evaluate(model: CostModel, table: dict, groups, default=(tri.MAP_LAMBDA, 16)) -> dict:
+def evaluate(model: CostModel, table: dict, groups, default=DEFAULT) -> dict:
     """Mean regret t(pick)/t(best) - 1 over groups for the model, the fixed
     default and the mean random candidate, plus the time a pick takes."""
     reg_model, reg_default, reg_random = [], [], []
@@ -194,6 +201,23 @@ def evaluate(model: CostModel, table: dict, groups, default=(tri.MAP_LAMBDA, 16)
     return {"regret_model": float(np.mean(reg_model)), "regret_default": float(np.mean(reg_default)),
             "regret_random": float(np.mean(reg_random)), "picks": picks, "pick_seconds": pick_s,
             "exhaustive_timed_ms_per_group": tune_ms}
+
+
+def evaluate_loo(table: dict, steps: int = 3000) -> dict:
+    """Leave one configuration out: for each group, train on all the others
+    and pick for it.  Mean regrets of the model and of the fixed default."""
+    keys = sorted(table["groups"])
+    reg_model, reg_default, picks = [], [], {}
+    for gkey in keys:
+        X, y = dataset(table, [k for k in keys if k != gkey])
+        model, _ = train(X, y, steps=steps)
+        res = evaluate(model, table, [gkey])
+        reg_model.append(res["regret_model"])
+        reg_default.append(res["regret_default"])
+        picks[gkey] = res["picks"][gkey]
+    return {"loo_regret_model": float(np.mean(reg_model)), "loo_regret_default": float(np.mean(reg_default)),
+            "loo_model_better_or_equal": int(sum(a <= b for a, b in zip(reg_model, reg_default))),
+            "loo_groups": len(keys), "loo_picks": picks}
 
 
 def main(argv=None):
@@ -227,9 +251,10 @@ def main(argv=None):
         res = evaluate(model, table, held)
         res["train_loss"] = loss
         res["train_rows"] = int(len(X))
+        res.update(evaluate_loo(table, steps=args.steps))
         with open(args.model, "w") as f:
             json.dump({"model": model.to_json(), "eval": res}, f, indent=1)
-        print(json.dumps({k: v for k, v in res.items() if k != "picks"}, indent=1))
+        print(json.dumps({k: v for k, v in res.items() if not k.endswith("picks")}, indent=1))
 
 
 if __name__ == "__main__":
