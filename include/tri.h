@@ -169,14 +169,17 @@ TRI_API int tri_edm_workspace_size(uint32_t n, uint32_t d, int prec, size_t *byt
  * stages); larger sizes give TRI_ERANGE.
  *
  *   tri_edm_prepare: clears the workspace header, then writes the FP32 row
- *     norms |x_i|^2 (summed to ~48 bits as FP32 pairs) and the BF16 split planes (hi, lo or hi,
- *     mid, lo; K zero-padded to a multiple of 64).
+ *     norms |x_i|^2 (summed to ~48 bits as FP32 pairs) and the BF16 split
+ *     planes (hi, lo or hi, mid, lo; K zero-padded to a multiple of 64).
  *   tri_edm_gram: tensor-core Gram term, d^2 = |x_i|^2 + |x_j|^2 - 2 x_i.x_j,
  *     clamped at 0, square root stored to out (packed, FP32); pairs with
  *     d^2 < tau (|x_i|^2 + |x_j|^2) appended to the workspace's flag list.
- *     map: TRI_MAP_LAMBDA (tiles in lambda order) or TRI_MAP_BB.  A device
- *     wait that exceeds 2 s sets the workspace status word to TRI_ETIMEOUT
- *     and the kernel returns.
+ *     map: TRI_MAP_LAMBDA (2 x 2 blocks of tiles in lambda order) or
+ *     TRI_MAP_BB.  Runs as clusters of two CTAs (tcgen05 cta_group::2).  A
+ *     device wait that exceeds 2 s sets the workspace status word (int at
+ *     byte 8) to TRI_ETIMEOUT and the kernel returns; if the two CTAs of a
+ *     pair cannot share their tensor-memory address the word becomes
+ *     TRI_ECUDA and the pair does no work.
  *   tri_edm_fixup: recomputes the flagged pairs in FP64 by direct differences
  *     (or, when the list overflowed, every pair whose stored distance passes a
  *     slightly wider flag test) and writes the flag count to *n_flagged

@@ -58,9 +58,9 @@ constexpr int STG_ROWS = 8;                // rows staged at a time by a row gro
 constexpr int STG_LD = TILE + 4;           // staging row: 128 distances shifted by the row's 16-byte phase
 constexpr int STG_FLOATS = STG_ROWS * STG_LD;  // one staging buffer
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
-constexpr int TQ = 8;                      // tile queue slots (producer -> MMA and epilogue)
-constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last tile
-constexpr uint32_t STATIC_PCT = 80;        // share of the tiles assigned up front, in contiguous runs
+constexpr int TQ = 8;                      // unit queue slots (producer -> MMA and epilogues, both CTAs)
+constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last unit
+constexpr uint32_t STATIC_PCT = 80;        // share of the units assigned up front, in contiguous runs per pair
 constexpr uint32_t DYN_CHUNK = 2;          // units per grab from the global counter afterwards
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int MAX_STAGES = 12;             // B ring depth cap (16 KB stages)
