@@ -336,6 +336,48 @@ TRI_API int tri_mlp_argmin(const float *theta, const float *X, uint32_t B, uint3
                    uint32_t H2, uint32_t *best, void *workspace, size_t ws_bytes,
                    void *stream);
 
+/*
+ * Map and rho selection from the learned cost model (not in the paper).
+ * Candidates of a (kernel, n, d) configuration are the autotuner's: for EDM
+ * the maps LAMBDA, LAMBDA_PDELTA, BB, RB, REC, UTM, for the Life step the
+ * same without UTM, for the triplet energy LAMBDA and BB; each with rho in
+ * {8, 16, 32}; REC only where the block rows are a power of two.  Their
+ * TRI_SELECT_FEATURES features: log2 n, log2 d, log2 rho, log2 of the blocks
+ * the map launches, kernel one-hot (EDM, CA, AT), map one-hot (LAMBDA,
+ * LAMBDA_PDELTA, BB, RB, REC, UTM), log2 of the tile side (4 rho for EDM
+ * and CA, rho for AT).
+ *
+ *   tri_select_features: host only.  Writes the candidates (maps outer, rho
+ *     inner) to maps[] / rhos[] and their raw features to X [count][F]
+ *     (FP32), count <= TRI_SELECT_MAX_CANDIDATES.
+ *   tri_select: standardises the features with the model's mu and sd (host
+ *     FP64), evaluates the MLP on the device (tri_mlp_argmin, theta on the
+ *     device in tri_mlp layout with F = TRI_SELECT_FEATURES) and writes the
+ *     candidate of smallest predicted log time (relative to the default
+ *     candidate) to *map and *rho.  Synchronises `stream`.  A NULL model or
+ *     theta gives the library default (TRI_MAP_LAMBDA, rho 16) with no device
+ *     work.  workspace: tri_select_workspace_size bytes, 256-byte aligned.
+ *   tri_sync_status: synchronises `stream` and reads one device status word
+ *     (the tensor-core workspace's int at byte 8, the batched EDM's ws[0])
+ *     into *value.
+ *   Errors: TRI_EINVAL (null pointers, n = 0, unknown kernel), TRI_ENOSPACE,
+ *   TRI_ECUDA.
+ */
+#define TRI_SELECT_FEATURES 14
+#define TRI_SELECT_MAX_CANDIDATES 18
+typedef enum { TRI_KERNEL_EDM = 0, TRI_KERNEL_CA = 1, TRI_KERNEL_AT = 2 } tri_kernel;
+typedef struct {
+    const float *theta;     /* device, tri_mlp parameter layout */
+    uint32_t h1, h2;        /* hidden widths */
+    const double *mu, *sd;  /* host, TRI_SELECT_FEATURES each */
+} tri_cost_model;
+TRI_API int tri_select_features(int kernel, uint32_t n, uint32_t d, float *X, int *maps, uint32_t *rhos,
+                                uint32_t *count);
+TRI_API int tri_select_workspace_size(uint32_t h1, uint32_t h2, size_t *bytes);
+TRI_API int tri_select(const tri_cost_model *model, int kernel, uint32_t n, uint32_t d, int *map, uint32_t *rho,
+                       void *workspace, size_t ws_bytes, void *stream);
+TRI_API int tri_sync_status(const int *status, int *value, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

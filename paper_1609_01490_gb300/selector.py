@@ -133,16 +133,13 @@ class CostModel:
         return pred.cpu().numpy()
 
     def pick(self, kernel: str, n: int, d: int):
-        """(map, rho) with the smallest predicted time (argmin on the GPU)."""
-        cands = candidates(kernel, n, d)
-        X = np.stack([features(kernel, n, d, m, r) for m, r in cands])
+        """(map, rho) with the smallest predicted time: features,
+        standardisation and the argmin all behind the library's tri_select."""
         dev = torch.device("cuda")
-        Xd = torch.from_numpy(self.standardise(X)).to(dev)
-        th = torch.from_numpy(self.theta).to(dev)
-        best = torch.zeros(1, dtype=torch.int32, device=dev)
-        ws = torch.empty(tri.tri_mlp_workspace_size(len(X), H1, H2) // 4 + 1, device=dev)
-        tri.tri_mlp_argmin(th, Xd, best, H1, H2, ws)
-        return cands[int(best.item())]
+        if self._dev is None:
+            self._dev = torch.from_numpy(self.theta).to(dev)
+        ws = torch.empty(tri.tri_select_workspace_size(H1, H2) // 4 + 64, device=dev)
+        return tri.tri_select(self._dev, H1, H2, self.mu, self.sd, KERNELS.index(kernel), n, d, ws)
 
     def to_json(self) -> dict:
         return {"theta": self.theta.tolist(), "mu": self.mu.tolist(), "sd": self.sd.tolist(), "h1": H1,

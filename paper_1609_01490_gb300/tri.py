@@ -33,10 +33,19 @@ FP32, BF16X3, BF16X6 = range(3)
 BODY_DUMMY, BODY_SENTINEL, BODY_COUNT = range(3)
 LIFE_BIRTH = 1 << 3
 LIFE_SURVIVE = (1 << 2) | (1 << 3)
+KERNEL_EDM, KERNEL_CA, KERNEL_AT = range(3)
+SELECT_FEATURES, SELECT_MAX_CANDIDATES = 14, 18
 
 _u32, _u64, _i32, _sz, _vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
 _f32, _f64 = ctypes.c_float, ctypes.c_double
 _szp = ctypes.POINTER(ctypes.c_size_t)
+
+
+class CostModelStruct(ctypes.Structure):
+    """tri_cost_model: device parameters, hidden widths, host standardisation."""
+    _fields_ = [("theta", _vp), ("h1", _u32), ("h2", _u32), ("mu", ctypes.POINTER(_f64)),
+                ("sd", ctypes.POINTER(_f64))]
+
 
 _SIGS = {
     "tri_status_string": ([_i32], ctypes.c_char_p),
@@ -61,6 +70,10 @@ _SIGS = {
     "tri_mlp_grad": ([_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp, _sz, _vp], _i32),
     "tri_mlp_adam": ([_vp, _vp, _vp, _vp, _u32, _u32, _f32, _f32, _f32, _f32, _vp], _i32),
     "tri_mlp_argmin": ([_vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _sz, _vp], _i32),
+    "tri_select_features": ([_i32, _u32, _u32, _vp, _vp, _vp, _vp], _i32),
+    "tri_select_workspace_size": ([_u32, _u32, _szp], _i32),
+    "tri_select": ([ctypes.POINTER(CostModelStruct), _i32, _u32, _u32, _vp, _vp, _vp, _sz, _vp], _i32),
+    "tri_sync_status": ([_vp, _vp, _vp], _i32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -252,3 +265,42 @@ def tri_mlp_argmin(theta, X, best, H1: int, H2: int, workspace, stream=None) -> 
     p, nb = _ws(workspace)
     _check("tri_mlp_argmin", _lib.tri_mlp_argmin(_ptr(theta), _ptr(X), B, F, H1, H2, _ptr(best), p, nb,
                                                  _stream(stream)))
+
+
+def tri_select_features(kernel: int, n: int, d: int):
+    """Host only: (X [count][14] FP32 raw features, maps, rhos) of the candidates."""
+    import numpy as np
+    X = np.zeros((SELECT_MAX_CANDIDATES, SELECT_FEATURES), dtype=np.float32)
+    maps = np.zeros(SELECT_MAX_CANDIDATES, dtype=np.int32)
+    rhos = np.zeros(SELECT_MAX_CANDIDATES, dtype=np.uint32)
+    count = ctypes.c_uint32(0)
+    _check("tri_select_features", _lib.tri_select_features(kernel, n, d, X.ctypes.data, maps.ctypes.data,
+                                                           rhos.ctypes.data, ctypes.addressof(count)))
+    c = count.value
+    return X[:c].copy(), [int(v) for v in maps[:c]], [int(v) for v in rhos[:c]]
+
+
+def tri_select_workspace_size(h1: int, h2: int) -> int:
+    return _size(_lib.tri_select_workspace_size, h1, h2)
+
+
+def tri_select(theta, h1: int, h2: int, mu, sd, kernel: int, n: int, d: int, workspace, stream=None):
+    """(map, rho) picked by the cost model (theta on the device, mu and sd host
+    FP64 arrays); theta None gives the library default.  Synchronises the stream."""
+    import numpy as np
+    mu64 = np.ascontiguousarray(mu, dtype=np.float64)
+    sd64 = np.ascontiguousarray(sd, dtype=np.float64)
+    model = CostModelStruct(_ptr(theta) if theta is not None else None, h1, h2,
+                            mu64.ctypes.data_as(ctypes.POINTER(_f64)), sd64.ctypes.data_as(ctypes.POINTER(_f64)))
+    m, r = ctypes.c_int(0), ctypes.c_uint32(0)
+    p, nb = _ws(workspace)
+    _check("tri_select", _lib.tri_select(ctypes.byref(model), kernel, n, d, ctypes.addressof(m),
+                                         ctypes.addressof(r), p, nb, _stream(stream)))
+    return m.value, r.value
+
+
+def tri_sync_status(status, stream=None) -> int:
+    """Synchronise the stream and read one device status word (an int32 tensor element)."""
+    v = ctypes.c_int(0)
+    _check("tri_sync_status", _lib.tri_sync_status(_ptr(status), ctypes.addressof(v), _stream(stream)))
+    return v.value

@@ -70,3 +70,44 @@ def test_selector_model_roundtrip():
     model, _ = selector.train(X, y, steps=50)
     again = selector.CostModel.from_json(json.loads(json.dumps(model.to_json())))
     np.testing.assert_array_equal(model.predict(X), again.predict(X))
+
+
+def test_tri_select_matches_predicted_argmin():
+    # the library's tri_select (features, standardisation, MLP argmin) picks the
+    # candidate that the model's own predictions rank first
+    dev()
+    from paper_1609_01490_gb300 import selector, tri
+    table = json.load(open(TABLE))
+    X, y = selector.dataset(table, sorted(table["groups"]))
+    model, _ = selector.train(X, y, steps=300)
+    for kernel, n, d in (("edm", 65536, 3), ("edm", 4096, 128), ("ca", 8192, 1), ("at", 768, 3),
+                         ("edm", 1000, 3)):
+        cands = selector.candidates(kernel, n, d)
+        pred = model.predict(np.stack([selector.features(kernel, n, d, m, r) for m, r in cands]))
+        got = model.pick(kernel, n, d)
+        assert got in cands
+        k = cands.index(got)
+        # equal to the argmin, or tied with it within FP32 rounding of the forward pass
+        assert pred[k] <= pred.min() + 1e-5
+    # no model: the library default
+    import torch
+    ws = torch.empty(tri.tri_select_workspace_size(64, 64) // 4 + 64, device="cuda")
+    assert tri.tri_select(None, 64, 64, np.zeros(14), np.ones(14), tri.KERNEL_EDM, 4096, 3, ws) == \
+        (tri.MAP_LAMBDA, 16)
+    with pytest.raises(tri.TriError):
+        tri.tri_select(model._dev, 64, 64, model.mu, model.sd, tri.KERNEL_EDM, 4096, 3, ws[:8])
+
+
+def test_tri_sync_status_reads_the_gram_status_word():
+    # the Gram kernel's workspace status word (byte 8) reads TRI_OK after a run
+    import torch
+    dev()
+    from paper_1609_01490_gb300 import tri
+    n, d = 300, 16
+    x = torch.randn(n, d, device="cuda")
+    out = torch.empty(n * (n + 1) // 2, device="cuda")
+    ws = torch.empty(tri.tri_edm_workspace_size(n, d, tri.BF16X6), dtype=torch.uint8, device="cuda")
+    tri.tri_edm(x, out, map=tri.MAP_LAMBDA, prec=tri.BF16X6, workspace=ws)
+    assert tri.tri_sync_status(ws[8:12].view(torch.int32)) == tri.TRI_OK
+    st = torch.tensor([tri.TRI_ETIMEOUT], dtype=torch.int32, device="cuda")
+    assert tri.tri_sync_status(st) == tri.TRI_ETIMEOUT

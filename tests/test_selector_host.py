@@ -59,3 +59,21 @@ def test_committed_sweep_table(sel):
     train, held = sel.split_groups(table)
     assert sorted(train + held) == sorted(groups) and len(held) == round(0.2 * len(groups))
     assert sel.split_groups(table) == (train, held)
+
+
+def test_library_features_match_selector(sel):
+    # tri_select_features (host code in the library) and the trainer's features
+    # list the same candidates in the same order with the same values
+    from paper_1609_01490_gb300 import tri
+    for kernel in ("edm", "ca", "at"):
+        for n, d in ((2048, 3), (1000, 1), (4096, 128), (65536, 3), (96, 8)):
+            X, maps, rhos = tri.tri_select_features(sel.KERNELS.index(kernel), n, d)
+            cands = sel.candidates(kernel, n, d)
+            assert list(zip(maps, rhos)) == cands
+            ref = np.stack([sel.features(kernel, n, d, m, r) for m, r in cands]).astype(np.float32)
+            np.testing.assert_allclose(X, ref, rtol=1e-6, atol=1e-6)
+    with pytest.raises(tri.TriError):
+        tri.tri_select_features(7, 100, 3)
+    with pytest.raises(tri.TriError):
+        tri.tri_select_features(0, 0, 3)
+    assert tri.tri_select_workspace_size(64, 64) >= 1280
