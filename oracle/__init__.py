@@ -21,6 +21,10 @@ Parity status per function (which pin ties it to something outside itself):
   at_energy                 pinned: equilateral, collinear and right-isosceles
                             closed forms; invariance under rigid motion and
                             permutation.
+  collide_*                 pinned: exact integer brute force on inputs where
+                            FP32 is exact, a touching lattice (closed-form
+                            neighbour counts), an interval sweep in 1-D,
+                            coincident and isolated spheres.
   mlp_*                     pinned: central finite differences of the loss, a
                             hand-solved one-unit network, the sign property of
                             the first Adam step.
@@ -57,6 +61,9 @@ def lib():
         L.orc_ca_run.argtypes = [vp, vp, i64, i64, ctypes.c_uint32, ctypes.c_uint32, i64]
         L.orc_at_energy.argtypes = [vp, i64, ctypes.c_double, vp]
         L.orc_at_energy.restype = ctypes.c_double
+        L.orc_collide_rows.argtypes = [vp, vp, i64, i64, i64, vp]
+        L.orc_collide_pairs.argtypes = [vp, vp, i64, i64, i64, vp, vp, vp]
+        L.orc_collide_count_of.argtypes = [vp, vp, i64, i64, vp, i64, vp]
         del u32p
         _lib = L
     return _lib
@@ -169,6 +176,51 @@ def at_energy(p: np.ndarray, nu: float = 1.0):
     a = np.zeros(1, dtype=np.float64)
     e = lib().orc_at_energy(_p(p), p.shape[0], float(nu), _p(a))
     return float(e), float(a[0])
+
+
+# ------------------------------------------------------------- collide ----
+def _spheres(c: np.ndarray, r: np.ndarray):
+    c = np.ascontiguousarray(c, dtype=np.float32)
+    if c.ndim == 1:
+        c = c[:, None]
+    r = np.ascontiguousarray(r, dtype=np.float32)
+    assert r.shape == (c.shape[0],)
+    return c, r
+
+
+def collide_pairs(c: np.ndarray, r: np.ndarray, r0: int = 0, r1: int | None = None):
+    """Colliding pairs (i, j), i > j, r0 <= i < r1, in increasing (i, j)
+    (Section 5, test 3; the FP32 test s <= (r_i + r_j)^2 of oracle.c)."""
+    c, r = _spheres(c, r)
+    n, dim = c.shape
+    r1 = n if r1 is None else r1
+    hits = np.zeros(max(r1 - r0, 0), dtype=np.int64)
+    if r1 > r0:
+        lib().orc_collide_rows(_p(c), _p(r), dim, r0, r1, _p(hits))
+    off = np.concatenate([[0], np.cumsum(hits)]).astype(np.int64)
+    pi = np.empty(int(off[-1]), dtype=np.uint32)
+    pj = np.empty(int(off[-1]), dtype=np.uint32)
+    if len(pi):
+        lib().orc_collide_pairs(_p(c), _p(r), dim, r0, r1, _p(off), _p(pi), _p(pj))
+    return pi, pj
+
+
+def collide_counts(c: np.ndarray, r: np.ndarray):
+    """(per-sphere collision counts, pairs i, pairs j) over all pairs."""
+    c, r = _spheres(c, r)
+    pi, pj = collide_pairs(c, r)
+    n = c.shape[0]
+    cnt = np.bincount(pi, minlength=n) + np.bincount(pj, minlength=n)
+    return cnt.astype(np.uint32), pi, pj
+
+
+def collide_count_of(c: np.ndarray, r: np.ndarray, idx) -> np.ndarray:
+    """Collision counts of the listed spheres alone, each against all others."""
+    c, r = _spheres(c, r)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(len(idx), dtype=np.int64)
+    lib().orc_collide_count_of(_p(c), _p(r), c.shape[0], c.shape[1], _p(idx), len(idx), _p(out))
+    return out
 
 
 # ----------------------------------------------------------------- MLP ----

@@ -226,3 +226,75 @@ double orc_at_energy(const float *p, int64_t n, double nu, double *abs_sum)
         *abs_sum = ea;
     return e;
 }
+
+/* ------------------------------------------------------------------------
+ * Section 5, test 3: collision detection of N spheres with random radii.
+ * Spheres i and j (i > j) collide when the distance between their centres is
+ * at most r_i + r_j (touching counts), tested on squares so that no root is
+ * taken:
+ *     s = sum_k (c_i,k - c_j,k)^2  (k = 0 .. dim-1, added in increasing k),
+ *     collide  <=>  s <= (r_i + r_j)^2.
+ * The paper fixes no precision.  Because this floating-point test decides an
+ * integer result, it is taken here in FP32, the precision of the GPU path:
+ * every difference, square, sum and the comparison are single IEEE FP32
+ * operations rounded to nearest, in the order written above (the build
+ * turns contraction into fused multiply-adds off).  Centres are row-major
+ * [n][dim].
+ * ------------------------------------------------------------------------ */
+static int orc_collide_hit(const float *c, const float *r, int64_t dim, int64_t i, int64_t j)
+{
+    float s = 0.0f;
+    for (int64_t k = 0; k < dim; ++k) {
+        float dk = c[i * dim + k] - c[j * dim + k];
+        float sq = dk * dk;
+        s = k == 0 ? sq : s + sq;
+    }
+    float rr = r[i] + r[j];
+    float rr2 = rr * rr;
+    return s <= rr2;
+}
+
+/* hits[i - r0] = number of j < i colliding with sphere i, for r0 <= i < r1. */
+void orc_collide_rows(const float *c, const float *r, int64_t dim, int64_t r0, int64_t r1, int64_t *hits)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = r0; i < r1; ++i) {
+        int64_t h = 0;
+        for (int64_t j = 0; j < i; ++j)
+            h += orc_collide_hit(c, r, dim, i, j);
+        hits[i - r0] = h;
+    }
+}
+
+/* The colliding pairs of rows r0 <= i < r1 in increasing (i, j): row i writes
+ * its pairs from position off[i - r0] (the exclusive prefix sum of the row
+ * counts above). */
+void orc_collide_pairs(const float *c, const float *r, int64_t dim, int64_t r0, int64_t r1, const int64_t *off,
+                       uint32_t *pi, uint32_t *pj)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = r0; i < r1; ++i) {
+        int64_t q = off[i - r0];
+        for (int64_t j = 0; j < i; ++j)
+            if (orc_collide_hit(c, r, dim, i, j)) {
+                pi[q] = (uint32_t)i;
+                pj[q] = (uint32_t)j;
+                ++q;
+            }
+    }
+}
+
+/* For each listed sphere idx[t]: the number of other spheres it collides
+ * with (both j < i and j > i), for sampled checks of per-sphere counts. */
+void orc_collide_count_of(const float *c, const float *r, int64_t n, int64_t dim, const int64_t *idx, int64_t k,
+                          int64_t *out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < k; ++t) {
+        int64_t i = idx[t], h = 0;
+        for (int64_t j = 0; j < n; ++j)
+            if (j != i)
+                h += j < i ? orc_collide_hit(c, r, dim, i, j) : orc_collide_hit(c, r, dim, j, i);
+        out[t] = h;
+    }
+}
