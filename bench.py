@@ -311,6 +311,37 @@ def run_suite(args):
           "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
                        "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"}})
 
+    # Section 5, test 3: collision detection of 65,536 spheres with about 4
+    # contacts each, 1-D and 3-D, under each map, with the paper's block shape
+    # (one pair per thread) and with 4 x 4 and 8 x 8 pairs per thread
+    n = 65536
+    npairs = torch.zeros(1, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(n, dtype=torch.int32, device=dev)
+    plist = torch.zeros((4 * n, 2), dtype=torch.int32, device=dev)
+    P = n * (n - 1) // 2
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * clk * 1e6 / 1e12  # one FP32 result per lane per clock
+    for dim in (1, 3):
+        cs, rs = inputs.spheres(n, dim)
+        cd, rd = torch.from_numpy(cs).to(dev), torch.from_numpy(rs).to(dev)
+        ops = 4 if dim == 1 else 10  # FP32 sub, mul, add per pair (no fused multiply-add)
+        for reg in (1, 4, 8):
+            maps = [("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB), ("rec", tri.MAP_REC)]
+            if reg == 1:
+                maps.append(("utm", tri.MAP_UTM))
+            t = {nm: graph_ms(lambda: tri.tri_collide(cd, rd, npairs, count=cnt, pairs=plist, map=m, rho=16,
+                                                      reg=reg), 5) for nm, m in maps}
+            top = ops * P / (t["lambda"] * 1e-3) / 1e12
+            emit({"row": f"collide_{dim}d_n65536_reg{reg}", "metric": "pairs/s", "unit": "pairs/s",
+                  "value": P / (t["lambda"] * 1e-3),
+                  "config": {"workload": f"spheres_{dim}d_n65536_kappa4", "rho": 16, "reg": reg,
+                             "pairs_per_thread": reg * reg}, "ms": t, "contacts": int(npairs.item()),
+                  "I_bb_over_lambda": t["bb"] / t["lambda"],
+                  "roofline": {"bound": "alu", "achieved": top, "peak": alu_peak, "unit": "TOP/s",
+                               "frac": top / alu_peak,
+                               "note": f"{ops} FP32 operations per pair; peak one result per FP32 lane per clock"}})
+        del cd, rd
+    del npairs, cnt, plist
+
     # a9: 1000 uneven EDM triangles: one persistent launch vs 1000 tri_edm launches (both in CUDA graphs)
     sizes = inputs.batched_sizes(1000, seed=1609)
     xc, pt_off = inputs.batched_points(sizes, 64, seed=1609)

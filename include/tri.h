@@ -257,6 +257,37 @@ TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
                 void *stream);
 
 /*
+ * tri_collide -- collision detection of N spheres (Section 5, test 3): every
+ * pair i > j whose centres lie at most r_i + r_j apart (touching counts).
+ * The test is taken on squares, s = sum_k (c[i][k] - c[j][k])^2 added in
+ * increasing k, collide <=> s <= (r_i + r_j)^2, each step one FP32 operation
+ * rounded to nearest (no fused multiply-add), so any implementation that
+ * takes the same steps reaches the same decisions bit for bit.
+ *   centres (device, FP32) row-major [n][dim], dim in {1, 2, 3}; radii
+ *   (device, FP32) [n].
+ *   map: any tri_map.  rho in {8, 16, 32}; reg in {1, 4, 8} (0 picks 4;
+ *   8 only with rho <= 16): blocks of rho x rho threads, each thread reg x reg
+ *   pairs of an S x S tile, S = rho*reg, whose 2 S spheres are staged in
+ *   shared memory (the paper's shared-memory test).  UTM (a thread-space map)
+ *   runs one pair per thread from global memory instead; reg is ignored there.
+ *   count (device uint32 [n], may be NULL): zeroed by the call, then
+ *   count[i] = the number of spheres sphere i collides with.
+ *   n_pairs (device uint64, required): zeroed by the call, then the number of
+ *   colliding pairs.
+ *   pairs (device uint32 [pair_cap][2], may be NULL when pair_cap = 0): the
+ *   first min(n_pairs, pair_cap) colliding pairs found, as (i, j) with i > j,
+ *   in no particular order; the caller compares n_pairs with pair_cap to see
+ *   whether the list is complete.
+ *   Errors: TRI_EINVAL (null n_pairs, null centres/radii with n > 0, pairs NULL with pair_cap >
+ *   0, dim or rho or reg or map out of range), TRI_ERANGE (too many blocks
+ *   for the map; REC with a block count that is not a power of two),
+ *   TRI_ECUDA.  n = 0 only zeroes n_pairs.
+ */
+TRI_API int tri_collide(const float *centres, const float *radii, uint32_t n, uint32_t dim, int map,
+                        uint32_t rho, uint32_t reg, uint32_t *count, uint32_t *pairs, uint64_t pair_cap,
+                        unsigned long long *n_pairs, void *stream);
+
+/*
  * tet_map -- map blocks onto the discrete tetrahedron (Section 6): block
  * omega -> (layer, row, col), layer >= row >= col, with the layer taken from
  * the real root of x^3 + 3x^2 + 2x - 6 omega = 0 (an FP32 estimate plus an

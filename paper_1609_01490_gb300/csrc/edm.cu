@@ -3,6 +3,7 @@
 // triangles in one persistent launch.
 #include <cuda_runtime.h>
 
+#include "f32x2.cuh"
 #include "tri_internal.h"
 #include "tri_maps.cuh"
 
@@ -11,36 +12,6 @@ using namespace tri;
 namespace {
 
 constexpr int KC = 32;  // features staged per shared-memory pass
-
-// One S x S pair tile, S = RHO*R, of the triangle over points x[0..n) (row-major,
-// d features): rows i0 = bi*S.., columns j0 = bj*S...  Thread (ty, tx) owns
-// rows ty + u*RHO and columns tx + v*RHO (u, v < R), so a warp's stores for
-// fixed (u, v) fall on consecutive columns of one or two rows.
-// Two FP32 lanes per instruction (IEEE round-to-nearest in each lane): the
-// same results as two scalar subtractions and fused multiply-adds.
-__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
-{
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
-{
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c)
-{
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 
 // Row pitch of the staged column points: even, so that a thread's two
 // adjacent columns load as one 8-byte word.

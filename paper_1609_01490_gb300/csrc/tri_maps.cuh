@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/tri.h"
 
@@ -241,6 +242,56 @@ inline uint64_t isqrt_ceil(uint64_t v)
         if (t * t <= v) r = t;
     }
     return r * r == v ? r : r + 1;
+}
+
+// The launches of a 2-D block map over m block rows: go(tag, grid, bm) is
+// called once per launch (REC: once per level) with tag an
+// std::integral_constant holding the kernel's MAP; returns a tri_status.
+template <class Go>
+int map_launches(int map, uint32_t m, Go &&go)
+{
+    using tri::BlockMap;
+    BlockMap bm{};
+    bm.m = m;
+    bm.nblocks = tri::T2(m);
+    cudaError_t e = cudaSuccess;
+    switch (map) {
+    case TRI_MAP_LAMBDA:
+        if (bm.nblocks > 0xFFFFFFFFull) return TRI_ERANGE;
+        e = go(std::integral_constant<int, tri::MAP_LAMBDA>{}, linear_grid(bm.nblocks), bm);
+        break;
+    case TRI_MAP_LAMBDA_PDELTA: {
+        if (bm.nblocks > 0xFFFFFFFFull) return TRI_ERANGE;
+        const uint64_t mp = isqrt_ceil(bm.nblocks);
+        if (mp > 65535) return TRI_ERANGE;
+        e = go(std::integral_constant<int, tri::MAP_LAMBDA_PD>{}, dim3((unsigned)mp, (unsigned)mp), bm);
+        break;
+    }
+    case TRI_MAP_BB:
+        if (m > 65535) return TRI_ERANGE;
+        e = go(std::integral_constant<int, tri::MAP_BB>{}, dim3(m, m), bm);
+        break;
+    case TRI_MAP_RB: {
+        const uint32_t h = (m & 1u) ? (m + 1) / 2 : m / 2 + 1;
+        if (h > 65535) return TRI_ERANGE;
+        e = go(std::integral_constant<int, tri::MAP_RB>{}, dim3(m, h), bm);
+        break;
+    }
+    case TRI_MAP_REC: {
+        if (!is_pow2(m)) return TRI_ERANGE;
+        const uint32_t k = ilog2(m);
+        if (k > 0 && m / 2 > 65535) return TRI_ERANGE;
+        for (uint32_t l = 0; l <= k && e == cudaSuccess; ++l) {
+            bm.level = l;
+            const dim3 g = l == 0 ? dim3(m) : dim3(1u << (l - 1), m / 2);
+            e = go(std::integral_constant<int, tri::MAP_REC>{}, g, bm);
+        }
+        break;
+    }
+    default:
+        return TRI_EINVAL;
+    }
+    return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
 
 }  // namespace trihost

@@ -130,3 +130,27 @@ def batched_points(sizes: np.ndarray, d: int, seed: int = 1609):
     pt_off[1:] = np.cumsum(sizes)[:-1].astype(np.uint64)
     x = normal_f32(seed, int(sizes.sum()) * d).reshape(-1, d)
     return x, pt_off
+
+
+def sphere_radius_max(n: int, dim: int, kappa: float) -> float:
+    """Upper end a of the radius distribution U[0, a) that gives about kappa
+    contacts per sphere among n uniform centres in the unit box (boundary
+    effects ignored): two spheres meet when their centres lie within
+    r_i + r_j, a ball of volume V_dim(r_i + r_j); with E[(r_i + r_j)^3] =
+    3a^3/2, E[(r_i + r_j)^2] = 7a^2/6 and E[r_i + r_j] = a the expected count
+    is (n-1) E[V_dim] = kappa."""
+    if dim == 1:  # V = 2 s
+        return kappa / (2.0 * (n - 1))
+    if dim == 2:  # V = pi s^2
+        return math.sqrt(kappa / ((n - 1) * math.pi * 7.0 / 6.0))
+    return (kappa / ((n - 1) * (4.0 / 3.0) * math.pi * 1.5)) ** (1.0 / 3.0)  # V = 4/3 pi s^3
+
+
+def spheres(n: int, dim: int = 3, kappa: float = 4.0, seed: int = 1611):
+    """n spheres in the unit box (Section 5, test 3): centres U[0,1)^dim, FP32
+    row-major [n][dim]; radii U[0, a) in FP32 with a from sphere_radius_max,
+    about kappa contacts per sphere."""
+    c = uniform_f32(seed, n * dim).reshape(n, dim)
+    a = sphere_radius_max(max(n, 2), dim, kappa)
+    r = (uniform_f64(seed ^ 0x2545F491, n) * a).astype(np.float32)
+    return c, r

@@ -61,6 +61,7 @@ _SIGS = {
     "tri_edm_batched": ([_vp, _vp, _vp, _u32, _u32, _vp, _vp, _u32, _u32, _vp, _sz, _vp], _i32),
     "tri_edm_batched_workspace_size": ([_u32, _szp], _i32),
     "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
+    "tri_collide": ([_vp, _vp, _u32, _u32, _i32, _u32, _u32, _vp, _vp, _u64, _vp, _vp], _i32),
     "tet_map": ([_u32, _u32, _i32, _vp, _vp], _i32),
     "tet_at_energy": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp, _sz, _vp], _i32),
     "tet_at_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
@@ -202,6 +203,19 @@ def tri_edm_batched(x_cat, pt_off, n_k, out_cat, out_off, rho: int = 16, reg: in
 
 
 # -------------------------------------------------------------------- CA --
+def tri_collide(centres, radii, n_pairs, count=None, pairs=None, map: int = MAP_LAMBDA, rho: int = 16,
+                reg: int = 0, stream=None) -> None:
+    """Collision detection of the spheres (centres [n][dim] FP32, radii [n]):
+    n_pairs (uint64 [1]) gets the number of colliding pairs, count (int32 or
+    uint32 [n]) the per-sphere counts, pairs (int32 or uint32 [cap][2]) the
+    first cap pairs (i, j), i > j, in no particular order."""
+    n = centres.shape[0]
+    dim = centres.shape[1] if centres.dim() == 2 else 1
+    cap = pairs.shape[0] if pairs is not None else 0
+    _check("tri_collide", _lib.tri_collide(_ptr(centres), _ptr(radii), n, dim, map, rho, reg, _ptr(count),
+                                           _ptr(pairs), cap, _ptr(n_pairs), _stream(stream)))
+
+
 def tri_ca_step(inp, out, n: int, birth_mask: int = LIFE_BIRTH, survive_mask: int = LIFE_SURVIVE,
                 map: int = MAP_LAMBDA, rho: int = 16, stream=None) -> None:
     ld = inp.stride(0)
