@@ -222,159 +222,192 @@ def run_suite(args):
             best = min(best, a.elapsed_time(b) / reps)
         return best
 
+    only = set(args.only.split(",")) if args.only else None
+
+    def want(section):
+        return only is None or section in only
+
     def emit(d):
         d.setdefault("data", "synthetic")
         d.setdefault("peaks", {"source": peak_src})
         print(json.dumps(d), flush=True)
 
-    # a1-a4: the maps alone (sentinel body), n = 65536, rho = 16
-    n = 65536
-    out = torch.zeros(4, dtype=torch.int32, device=dev)
-    times = {}
-    for name, m, sq in (("lambda_X", tri.MAP_LAMBDA, tri.SQRT_X), ("lambda_R", tri.MAP_LAMBDA, tri.SQRT_R),
-                        ("lambda_N", tri.MAP_LAMBDA, tri.SQRT_N), ("lambda_pdelta_R", tri.MAP_LAMBDA_PDELTA, tri.SQRT_R),
-                        ("bb", tri.MAP_BB, tri.SQRT_R), ("rb", tri.MAP_RB, tri.SQRT_R),
-                        ("rec", tri.MAP_REC, tri.SQRT_R), ("utm", tri.MAP_UTM, tri.SQRT_R)):
-        times[name] = graph_ms(lambda: tri.tri_map_launch(m, sq, n, 16, True, tri.BODY_SENTINEL, out), 20)
-    elems = n * (n + 1) // 2
-    emit({"row": "map_only", "metric": "mapped elements/s", "unit": "elements/s",
-          "config": {"workload": "sentinel body (map cost only)", "n": n, "rho": 16},
-          "ms": times, "value": {k: elems / (v * 1e-3) for k, v in times.items()},
-          "I_bb_over": {k: times["bb"] / v for k, v in times.items()}})
+    if want("maps"):
+        # a1-a4: the maps alone (sentinel body), n = 65536, rho = 16
+        n = 65536
+        out = torch.zeros(4, dtype=torch.int32, device=dev)
+        times = {}
+        for name, m, sq in (("lambda_X", tri.MAP_LAMBDA, tri.SQRT_X), ("lambda_R", tri.MAP_LAMBDA, tri.SQRT_R),
+                            ("lambda_N", tri.MAP_LAMBDA, tri.SQRT_N), ("lambda_pdelta_R", tri.MAP_LAMBDA_PDELTA, tri.SQRT_R),
+                            ("bb", tri.MAP_BB, tri.SQRT_R), ("rb", tri.MAP_RB, tri.SQRT_R),
+                            ("rec", tri.MAP_REC, tri.SQRT_R), ("utm", tri.MAP_UTM, tri.SQRT_R)):
+            times[name] = graph_ms(lambda: tri.tri_map_launch(m, sq, n, 16, True, tri.BODY_SENTINEL, out), 20)
+        elems = n * (n + 1) // 2
+        emit({"row": "map_only", "metric": "mapped elements/s", "unit": "elements/s",
+              "config": {"workload": "sentinel body (map cost only)", "n": n, "rho": 16},
+              "ms": times, "value": {k: elems / (v * 1e-3) for k, v in times.items()},
+              "I_bb_over": {k: times["bb"] / v for k, v in times.items()}})
 
-    # a5: the paper-size EDM, N = 2048, d = 3, rho = 16 (8.4 MB output, L2-resident)
-    x = torch.from_numpy(inputs.edm_uniform_points(2048, 3, seed=1609)).to(dev)
-    o = torch.empty(2048 * 2049 // 2, dtype=torch.float32, device=dev)
-    t = {nm: graph_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=1), 200)
-         for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB),
-                       ("rec", tri.MAP_REC), ("utm", tri.MAP_UTM))}
-    P = 2048 * 2049 // 2
-    emit({"row": "edm_fp32_paper_size", "metric": "pairs/s", "unit": "pairs/s", "value": P / (t["lambda"] * 1e-3),
-          "config": {"workload": "edm_n2048_d3_uniform", "rho": 16, "reg": 1, "launches_per_graph": 200},
-          "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
-          "roofline": {"bound": "hbm", "achieved": 4.0 * P / (t["lambda"] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                       "frac": 4.0 * P / (t["lambda"] * 1e-3) / 1e9 / hbm,
-                       "note": "8.4 MB output stays in L2 across back-to-back launches"}})
+    if want("maps"):
+        # the square-root strategies of Section 4.1 over n (the map-only sweep
+        # of the paper's dummy-kernel test): time per launch of the sentinel
+        # body under lambda_X, lambda_R, lambda_N and the bounding box
+        sweep = {}
+        for n in (1024, 2048, 4096, 8192, 16384, 32768, 65536):
+            reps = max(3, min(200, (1 << 34) // (n * n)))
+            sweep[n] = {name: graph_ms(lambda: tri.tri_map_launch(m, sq, n, 16, True, tri.BODY_SENTINEL, out), reps)
+                        for name, m, sq in (("lambda_X", tri.MAP_LAMBDA, tri.SQRT_X),
+                                            ("lambda_R", tri.MAP_LAMBDA, tri.SQRT_R),
+                                            ("lambda_N", tri.MAP_LAMBDA, tri.SQRT_N),
+                                            ("bb", tri.MAP_BB, tri.SQRT_R))}
+        emit({"row": "map_sqrt_sweep", "metric": "ms per launch", "unit": "ms",
+              "config": {"workload": "sentinel body, rho = 16, n = 1024 ... 65536"},
+              "ms": sweep, "I_bb_over_lambda_R": {n: v["bb"] / v["lambda_R"] for n, v in sweep.items()},
+              "lambda_N_over_lambda_X": {n: v["lambda_N"] / v["lambda_X"] for n, v in sweep.items()},
+              "lambda_R_over_lambda_X": {n: v["lambda_R"] / v["lambda_X"] for n, v in sweep.items()}})
 
-    # a2/a5 at scale: N = 65536, d = 3 (store-bound, 8.6 GB of output) with the
-    # paper's block shape (one pair per thread, rho = 16) and with 4 x 4 pairs per thread
-    x = torch.from_numpy(inputs.edm_uniform_points(65536, 3, seed=1609)).to(dev)
-    o = torch.empty(65536 * 65537 // 2, dtype=torch.float32, device=dev)
-    P = 65536 * 65537 // 2
-    for reg in (1, 4):
-        t = {nm: graph_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=reg), 3)
+    if want("edm"):
+        # a5: the paper-size EDM, N = 2048, d = 3, rho = 16 (8.4 MB output, L2-resident)
+        x = torch.from_numpy(inputs.edm_uniform_points(2048, 3, seed=1609)).to(dev)
+        o = torch.empty(2048 * 2049 // 2, dtype=torch.float32, device=dev)
+        t = {nm: graph_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=1), 200)
              for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB),
-                           ("rec", tri.MAP_REC))}
-        gbs = 4.0 * P / (t["lambda"] * 1e-3) / 1e9
-        emit({"row": f"edm_fp32_n65536_d3_reg{reg}", "metric": "pairs/s", "unit": "pairs/s",
-              "value": P / (t["lambda"] * 1e-3),
-              "config": {"workload": "edm_n65536_d3_uniform", "rho": 16, "reg": reg,
-                         "pairs_per_thread": reg * reg}, "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
-              "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}})
-    del x, o
-    torch.cuda.empty_cache()
+                           ("rec", tri.MAP_REC), ("utm", tri.MAP_UTM))}
+        P = 2048 * 2049 // 2
+        emit({"row": "edm_fp32_paper_size", "metric": "pairs/s", "unit": "pairs/s", "value": P / (t["lambda"] * 1e-3),
+              "config": {"workload": "edm_n2048_d3_uniform", "rho": 16, "reg": 1, "launches_per_graph": 200},
+              "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
+              "roofline": {"bound": "hbm", "achieved": 4.0 * P / (t["lambda"] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": 4.0 * P / (t["lambda"] * 1e-3) / 1e9 / hbm,
+                           "note": "8.4 MB output stays in L2 across back-to-back launches"}})
 
-    # a6: triangular Life, n = 16384, 100 steps, rho = 16
-    n = 16384
-    a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)
-    b = torch.zeros_like(a)
-
-    def life(m):
-        def run():
-            for s in range(100):
-                src, dst = (a, b) if s % 2 == 0 else (b, a)
-                tri.tri_ca_step(src, dst, n, map=m, rho=16)
-        return run
-    t = {nm: graph_ms(life(m), 1) / 100 for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB),
-                                                      ("rb", tri.MAP_RB), ("rec", tri.MAP_REC))}
-    cells = n * (n + 1) // 2
-    gbs = 2.0 * cells / (t["lambda"] * 1e-3) / 1e9
-    emit({"row": "life_step", "metric": "cell updates/s", "unit": "cells/s", "value": cells / (t["lambda"] * 1e-3),
-          "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 16}, "ms_per_step": t,
-          "I_bb_over_lambda": t["bb"] / t["lambda"],
-          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                       "algorithmic_bytes_per_step": 2 * cells}})
-
-    # a7: Axilrod-Teller energy over the tetrahedral domain, N = 1536, rho = 16
-    n = 1536
-    p = torch.from_numpy(inputs.at_points(n, seed=1610)).to(dev)
-    e = torch.zeros(1, dtype=torch.float64, device=dev)
-    ws = torch.empty(max(tri.tet_at_workspace_size(n, 16, m) for m in (tri.MAP_LAMBDA, tri.MAP_BB)) // 8 + 1,
-                     dtype=torch.float64, device=dev)
-    t = {nm: graph_ms(lambda: tri.tet_at_energy(p, e, 1.0, m, 16, ws), 20)
-         for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB))}
-    trip = n * (n - 1) * (n - 2) // 6
-    tf = 40.0 * trip / (t["lambda"] * 1e-3) / 1e12
-    emit({"row": "at_energy", "metric": "triplets/s", "unit": "triplets/s", "value": trip / (t["lambda"] * 1e-3),
-          "config": {"workload": "at_n1536_uniform_unit_density", "rho": 16}, "ms": t,
-          "I_bb_over_lambda": t["bb"] / t["lambda"],
-          "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
-                       "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"}})
-
-    # Section 5, test 3: collision detection of 65,536 spheres with about 4
-    # contacts each, 1-D and 3-D, under each map, with the paper's block shape
-    # (one pair per thread) and with 4 x 4 and 8 x 8 pairs per thread
-    n = 65536
-    npairs = torch.zeros(1, dtype=torch.int64, device=dev)
-    cnt = torch.zeros(n, dtype=torch.int32, device=dev)
-    plist = torch.zeros((4 * n, 2), dtype=torch.int32, device=dev)
-    P = n * (n - 1) // 2
-    alu_peak = NUM_SMS * FP32_LANES_PER_SM * clk * 1e6 / 1e12  # one FP32 result per lane per clock
-    for dim in (1, 3):
-        cs, rs = inputs.spheres(n, dim)
-        cd, rd = torch.from_numpy(cs).to(dev), torch.from_numpy(rs).to(dev)
-        ops = 4 if dim == 1 else 10  # FP32 sub, mul, add per pair (no fused multiply-add)
-        for reg in (1, 4, 8):
-            maps = [("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB), ("rec", tri.MAP_REC)]
-            if reg == 1:
-                maps.append(("utm", tri.MAP_UTM))
-            t = {nm: graph_ms(lambda: tri.tri_collide(cd, rd, npairs, count=cnt, pairs=plist, map=m, rho=16,
-                                                      reg=reg), 5) for nm, m in maps}
-            top = ops * P / (t["lambda"] * 1e-3) / 1e12
-            emit({"row": f"collide_{dim}d_n65536_reg{reg}", "metric": "pairs/s", "unit": "pairs/s",
+    if want("edm"):
+        # a2/a5 at scale: N = 65536, d = 3 (store-bound, 8.6 GB of output) with the
+        # paper's block shape (one pair per thread, rho = 16) and with 4 x 4 pairs per thread
+        x = torch.from_numpy(inputs.edm_uniform_points(65536, 3, seed=1609)).to(dev)
+        o = torch.empty(65536 * 65537 // 2, dtype=torch.float32, device=dev)
+        P = 65536 * 65537 // 2
+        for reg in (1, 4):
+            t = {nm: graph_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=reg), 3)
+                 for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB),
+                               ("rec", tri.MAP_REC))}
+            gbs = 4.0 * P / (t["lambda"] * 1e-3) / 1e9
+            emit({"row": f"edm_fp32_n65536_d3_reg{reg}", "metric": "pairs/s", "unit": "pairs/s",
                   "value": P / (t["lambda"] * 1e-3),
-                  "config": {"workload": f"spheres_{dim}d_n65536_kappa4", "rho": 16, "reg": reg,
-                             "pairs_per_thread": reg * reg}, "ms": t, "contacts": int(npairs.item()),
-                  "I_bb_over_lambda": t["bb"] / t["lambda"],
-                  "roofline": {"bound": "alu", "achieved": top, "peak": alu_peak, "unit": "TOP/s",
-                               "frac": top / alu_peak,
-                               "note": f"{ops} FP32 operations per pair; peak one result per FP32 lane per clock"}})
-        del cd, rd
-    del npairs, cnt, plist
+                  "config": {"workload": "edm_n65536_d3_uniform", "rho": 16, "reg": reg,
+                             "pairs_per_thread": reg * reg}, "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
+                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}})
+        del x, o
+        torch.cuda.empty_cache()
 
-    # a9: 1000 uneven EDM triangles: one persistent launch vs 1000 tri_edm launches (both in CUDA graphs)
-    sizes = inputs.batched_sizes(1000, seed=1609)
-    xc, pt_off = inputs.batched_points(sizes, 64, seed=1609)
-    tri_len = sizes.astype(np.int64) * (sizes.astype(np.int64) + 1) // 2
-    out_off = np.zeros(len(sizes), dtype=np.uint64)
-    out_off[1:] = np.cumsum(tri_len)[:-1]
-    total = int(tri_len.sum())
-    xd = torch.from_numpy(xc).to(dev)
-    oc = torch.empty(total, dtype=torch.float32, device=dev)
-    pto = torch.from_numpy(pt_off.view(np.int64)).to(dev)
-    nk = torch.from_numpy(sizes.astype(np.int32)).to(dev)
-    oo = torch.from_numpy(out_off.view(np.int64)).to(dev)
-    wsb = torch.empty(tri.tri_edm_batched_workspace_size(1000) // 8 + 1, dtype=torch.int64, device=dev)
-    tb = {}
-    for rho in (8, 16, 32):
-        tb[f"persistent_rho{rho}"] = graph_ms(lambda: tri.tri_edm_batched(xd, pto, nk, oc, oo, rho=rho, reg=0,
-                                                                           workspace=wsb), 1)
-    views = [(xd[int(pt_off[k]): int(pt_off[k]) + int(sizes[k])], oc[int(out_off[k]): int(out_off[k]) + int(tri_len[k])])
-             for k in range(1000)]
+    if want("life"):
+        # a6: triangular Life, n = 16384, 100 steps, rho = 16
+        n = 16384
+        a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)
+        b = torch.zeros_like(a)
 
-    def separate():
-        for xv, ov in views:
-            tri.tri_edm(xv, ov, map=tri.MAP_LAMBDA, rho=16, reg=0)
-    tb["separate_1000_launches"] = graph_ms(separate, 1)
-    best = min(v for k, v in tb.items() if k.startswith("persistent"))
-    tf = 3.0 * 64 * total / (best * 1e-3) / 1e12
-    emit({"row": "edm_batched", "metric": "pairs/s", "unit": "pairs/s", "value": total / (best * 1e-3),
-          "config": {"workload": "1000 instances, N log-uniform [64, 8192], d = 64", "pairs": total}, "ms": tb,
-          "speedup_over_separate": tb["separate_1000_launches"] / best,
-          "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak}})
+        def life(m):
+            def run():
+                for s in range(100):
+                    src, dst = (a, b) if s % 2 == 0 else (b, a)
+                    tri.tri_ca_step(src, dst, n, map=m, rho=16)
+            return run
+        t = {nm: graph_ms(life(m), 1) / 100 for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB),
+                                                          ("rb", tri.MAP_RB), ("rec", tri.MAP_REC))}
+        cells = n * (n + 1) // 2
+        gbs = 2.0 * cells / (t["lambda"] * 1e-3) / 1e9
+        emit({"row": "life_step", "metric": "cell updates/s", "unit": "cells/s", "value": cells / (t["lambda"] * 1e-3),
+              "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 16}, "ms_per_step": t,
+              "I_bb_over_lambda": t["bb"] / t["lambda"],
+              "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                           "algorithmic_bytes_per_step": 2 * cells}})
+
+    if want("at"):
+        # a7: Axilrod-Teller energy over the tetrahedral domain, N = 1536, rho = 16
+        n = 1536
+        p = torch.from_numpy(inputs.at_points(n, seed=1610)).to(dev)
+        e = torch.zeros(1, dtype=torch.float64, device=dev)
+        ws = torch.empty(max(tri.tet_at_workspace_size(n, 16, m) for m in (tri.MAP_LAMBDA, tri.MAP_BB)) // 8 + 1,
+                         dtype=torch.float64, device=dev)
+        t = {nm: graph_ms(lambda: tri.tet_at_energy(p, e, 1.0, m, 16, ws), 20)
+             for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB))}
+        trip = n * (n - 1) * (n - 2) // 6
+        tf = 40.0 * trip / (t["lambda"] * 1e-3) / 1e12
+        emit({"row": "at_energy", "metric": "triplets/s", "unit": "triplets/s", "value": trip / (t["lambda"] * 1e-3),
+              "config": {"workload": "at_n1536_uniform_unit_density", "rho": 16}, "ms": t,
+              "I_bb_over_lambda": t["bb"] / t["lambda"],
+              "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                           "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"}})
+
+    if want("collide"):
+        # Section 5, test 3: collision detection of 65,536 spheres (smaller
+        # counts are for profiling) with about 4 contacts each, 1-D and 3-D,
+        # under each map, with the paper's block shape (one pair per thread)
+        # and with 4 x 4 and 8 x 8 pairs per thread
+        n = args.collide_n
+        npairs = torch.zeros(1, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(n, dtype=torch.int32, device=dev)
+        plist = torch.zeros((4 * n, 2), dtype=torch.int32, device=dev)
+        P = n * (n - 1) // 2
+        alu_peak = NUM_SMS * FP32_LANES_PER_SM * clk * 1e6 / 1e12  # one FP32 result per lane per clock
+        for dim in (1, 3):
+            cs, rs = inputs.spheres(n, dim)
+            cd, rd = torch.from_numpy(cs).to(dev), torch.from_numpy(rs).to(dev)
+            ops = 4 if dim == 1 else 10  # FP32 sub, mul, add per pair (no fused multiply-add)
+            for reg in (1, 4, 8):
+                maps = [("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB), ("rec", tri.MAP_REC)]
+                if reg == 1:
+                    maps.append(("utm", tri.MAP_UTM))
+                t = {nm: graph_ms(lambda: tri.tri_collide(cd, rd, npairs, count=cnt, pairs=plist, map=m, rho=16,
+                                                          reg=reg), 5) for nm, m in maps}
+                top = ops * P / (t["lambda"] * 1e-3) / 1e12
+                emit({"row": f"collide_{dim}d_n{n}_reg{reg}", "metric": "pairs/s", "unit": "pairs/s",
+                      "value": P / (t["lambda"] * 1e-3),
+                      "config": {"workload": f"spheres_{dim}d_n{n}_kappa4", "rho": 16, "reg": reg,
+                                 "pairs_per_thread": reg * reg}, "ms": t, "contacts": int(npairs.item()),
+                      "I_bb_over_lambda": t["bb"] / t["lambda"],
+                      "roofline": {"bound": "alu", "achieved": top, "peak": alu_peak, "unit": "TOP/s",
+                                   "frac": top / alu_peak,
+                                   "note": f"{ops} FP32 operations per pair; peak one result per FP32 lane per clock"}})
+            del cd, rd
+        del npairs, cnt, plist
+
+    if want("batched"):
+        # a9: 1000 uneven EDM triangles: one persistent launch vs 1000 tri_edm launches (both in CUDA graphs)
+        sizes = inputs.batched_sizes(1000, seed=1609)
+        xc, pt_off = inputs.batched_points(sizes, 64, seed=1609)
+        tri_len = sizes.astype(np.int64) * (sizes.astype(np.int64) + 1) // 2
+        out_off = np.zeros(len(sizes), dtype=np.uint64)
+        out_off[1:] = np.cumsum(tri_len)[:-1]
+        total = int(tri_len.sum())
+        xd = torch.from_numpy(xc).to(dev)
+        oc = torch.empty(total, dtype=torch.float32, device=dev)
+        pto = torch.from_numpy(pt_off.view(np.int64)).to(dev)
+        nk = torch.from_numpy(sizes.astype(np.int32)).to(dev)
+        oo = torch.from_numpy(out_off.view(np.int64)).to(dev)
+        wsb = torch.empty(tri.tri_edm_batched_workspace_size(1000) // 8 + 1, dtype=torch.int64, device=dev)
+        tb = {}
+        for rho in (8, 16, 32):
+            tb[f"persistent_rho{rho}"] = graph_ms(lambda: tri.tri_edm_batched(xd, pto, nk, oc, oo, rho=rho, reg=0,
+                                                                               workspace=wsb), 1)
+        views = [(xd[int(pt_off[k]): int(pt_off[k]) + int(sizes[k])], oc[int(out_off[k]): int(out_off[k]) + int(tri_len[k])])
+                 for k in range(1000)]
+
+        def separate():
+            for xv, ov in views:
+                tri.tri_edm(xv, ov, map=tri.MAP_LAMBDA, rho=16, reg=0)
+        tb["separate_1000_launches"] = graph_ms(separate, 1)
+        best = min(v for k, v in tb.items() if k.startswith("persistent"))
+        tf = 3.0 * 64 * total / (best * 1e-3) / 1e12
+        emit({"row": "edm_batched", "metric": "pairs/s", "unit": "pairs/s", "value": total / (best * 1e-3),
+              "config": {"workload": "1000 instances, N log-uniform [64, 8192], d = 64", "pairs": total}, "ms": tb,
+              "speedup_over_separate": tb["separate_1000_launches"] / best,
+              "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak}})
 
 
-# -------------------------------------------------------------- our arm -----
+    # -------------------------------------------------------------- our arm -----
+
+
 def main():
     global N_PTS, D_FEAT, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -389,6 +422,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_PTS, help="points (smaller cases are for profiling only)")
     ap.add_argument("--d", type=int, default=D_FEAT, help="features (smaller cases are for profiling only)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per other hot-path row instead")
+    ap.add_argument("--only", default="", help="suite sections to run (maps,edm,life,at,collide,batched)")
+    ap.add_argument("--collide-n", type=int, default=65536, help="spheres in the collision rows")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

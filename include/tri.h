@@ -265,8 +265,8 @@ TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
  * takes the same steps reaches the same decisions bit for bit.
  *   centres (device, FP32) row-major [n][dim], dim in {1, 2, 3}; radii
  *   (device, FP32) [n].
- *   map: any tri_map.  rho in {8, 16, 32}; reg in {1, 4, 8} (0 picks 4;
- *   8 only with rho <= 16): blocks of rho x rho threads, each thread reg x reg
+ *   map: any tri_map.  rho in {8, 16, 32}; reg in {1, 4, 8} (0 picks 8 for
+ *   rho <= 16 and 4 for rho = 32; 8 only with rho <= 16): blocks of rho x rho threads, each thread reg x reg
  *   pairs of an S x S tile, S = rho*reg, whose 2 S spheres are staged in
  *   shared memory (the paper's shared-memory test).  UTM (a thread-space map)
  *   runs one pair per thread from global memory instead; reg is ignored there.

@@ -55,104 +55,113 @@ __device__ __forceinline__ void record(const CollideOut &o, uint32_t i, uint32_t
 
 // One S x S pair tile, S = RHO*R: rows i0 = bi S + [0, S), columns
 // j0 = bj S + [0, S).  The 2 S spheres are staged transposed ([coordinate or
-// radius][sphere]); spheres past n get NaN centres, whose every test fails.
-// Thread (ty, tx) owns rows ty + u RHO (u < R) and, for R >= 2, the column
-// pairs 2 tx + 2 RHO v + {0, 1} (v < R/2), tested two at a time with f32x2
-// instructions; for R = 1 it owns column tx.  The fast path only asks
-// whether any of the thread's pairs hit; a thread that saw a hit (rare, and
-// always on the diagonal, where a sphere meets itself) re-tests its pairs one
-// by one with the same operations and records the valid ones (i < n, j < i).
-// Not inlined: every block map calls the same compiled body.
+// radius][sphere]), the rows with each value duplicated into both halves of
+// an 8-byte word.  Thread (ty, tx) owns rows ty + u RHO (u < R) and, for
+// R >= 2, the column pairs 2 tx + 2 RHO v + {0, 1} (v < R/2), tested two at a
+// time with f32x2 instructions, whose lanes round exactly as the scalar
+// operations of the reference order do.  The fast pass keeps one word: the
+// AND of the bits of q - s over all the thread's pairs; since q - s rounds to
+// a value >= 0 exactly when q >= s, a clear sign bit means some pair may hit
+// (or some input is NaN).  Only such threads (a few per contact, plus the
+// diagonal, where a sphere meets itself) repeat the packed pass, compare s
+// and q lane by lane and record the valid pairs (i < n, j < i).
+// Padding spheres past n sit at +inf (rows) and -inf (columns), so their
+// tests give s = inf and never flag.  For R = 1 each thread takes the scalar
+// test of its one pair.  Not inlined: every block map calls the same body.
 template <int RHO, int R, int DIM>
 __device__ __noinline__ void collide_tile(const float *__restrict__ c, const float *__restrict__ rad, uint32_t n,
                                           uint32_t bi, uint32_t bj, CollideOut o)
 {
     constexpr int S = RHO * R;
-    __shared__ float si[DIM + 1][S + 1];
-    __shared__ __align__(8) float sj[DIM + 1][S + 2];
+    constexpr int RC = R == 1 ? 1 : R / 2;
+    __shared__ f2 si[DIM + 1][S];                       // rows, duplicated
+    __shared__ __align__(8) float sj[DIM + 1][S + 2];   // columns
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RHO + tx;
     const uint64_t i0 = (uint64_t)bi * S, j0 = (uint64_t)bj * S;
-    const float qnan = __int_as_float(0x7fc00000);
-    // coalesced staging of S consecutive spheres: centres (S DIM floats) then radii
+    const float inf = __int_as_float(0x7f800000);
+    // coalesced staging of S consecutive spheres: centres (S DIM floats), then radii
     for (int t = tid; t < S * DIM; t += RHO * RHO) {
         const int r = t / DIM, k = t - r * DIM;
-        si[k][r] = i0 + r < n ? c[i0 * DIM + t] : qnan;
-        sj[k][r] = j0 + r < n ? c[j0 * DIM + t] : qnan;
+        const float a = i0 + r < n ? c[i0 * DIM + t] : inf;
+        si[k][r] = f2_pack(a, a);
+        sj[k][r] = j0 + r < n ? c[j0 * DIM + t] : -inf;
     }
     for (int t = tid; t < S; t += RHO * RHO) {
-        si[DIM][t] = i0 + t < n ? rad[i0 + t] : 0.0f;
+        const float a = i0 + t < n ? rad[i0 + t] : 0.0f;
+        si[DIM][t] = f2_pack(a, a);
         sj[DIM][t] = j0 + t < n ? rad[j0 + t] : 0.0f;
     }
     __syncthreads();
 
-    bool any = false;
     if constexpr (R == 1) {
-        float a[DIM + 1], b[DIM + 1];
+        float a[DIM + 1], b[DIM + 1], dummy;
 #pragma unroll
         for (int k = 0; k <= DIM; ++k) {
-            a[k] = si[k][ty];
+            f2_unpack(si[k][ty], a[k], dummy);
             b[k] = sj[k][tx];
         }
-        any = hit_scalar<DIM>(a, b);
+        const uint64_t i = i0 + ty, j = j0 + tx;
+        if (hit_scalar<DIM>(a, b) && i < n && j < i) record(o, (uint32_t)i, (uint32_t)j);
+        return;
     } else {
-        constexpr int RC = R / 2;
         f2 b2[RC][DIM + 1];
 #pragma unroll
         for (int v = 0; v < RC; ++v)
 #pragma unroll
-            for (int k = 0; k <= DIM; ++k)
-                b2[v][k] = *reinterpret_cast<const f2 *>(&sj[k][2 * tx + 2 * RHO * v]);
+            for (int k = 0; k <= DIM; ++k) b2[v][k] = *reinterpret_cast<const f2 *>(&sj[k][2 * tx + 2 * RHO * v]);
+        // s and q of the column pair v for row values a2, in the reference order
+        auto test = [&](const f2 *a2, int v, f2 &s, f2 &q) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const f2 dk = f2_sub(a2[k], b2[v][k]);
+                s = k == 0 ? f2_mul(dk, dk) : f2_add(s, f2_mul(dk, dk));
+            }
+            const f2 rr = f2_add(a2[DIM], b2[v][DIM]);
+            q = f2_mul(rr, rr);
+        };
+        uint32_t acc = 0xFFFFFFFFu;
 #pragma unroll
         for (int u = 0; u < R; ++u) {
             f2 a2[DIM + 1];
 #pragma unroll
-            for (int k = 0; k <= DIM; ++k) {
-                const float a = si[k][ty + u * RHO];
-                a2[k] = f2_pack(a, a);
-            }
+            for (int k = 0; k <= DIM; ++k) a2[k] = si[k][ty + u * RHO];
 #pragma unroll
             for (int v = 0; v < RC; ++v) {
-                f2 s = 0;
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    const f2 dk = f2_sub(a2[k], b2[v][k]);
-                    const f2 sq = f2_mul(dk, dk);
-                    s = k == 0 ? sq : f2_add(s, sq);
-                }
-                const f2 rr = f2_add(a2[DIM], b2[v][DIM]);
-                const f2 rr2 = f2_mul(rr, rr);
-                float s0, s1, q0, q1;
-                f2_unpack(s, s0, s1);
-                f2_unpack(rr2, q0, q1);
-                any |= (s0 <= q0) | (s1 <= q1);
+                f2 s, q;
+                test(a2, v, s, q);
+                const f2 d = f2_sub(q, s);
+                acc &= (uint32_t)d & (uint32_t)(d >> 32);
             }
         }
-    }
-    if (!any) return;
-    // slow path: exact per-pair re-test from shared memory
+        if ((int)acc < 0) return;
+        // some pair may hit: the same tests again, decided lane by lane
 #pragma unroll 1
-    for (int u = 0; u < R; ++u) {
-        const int ri = ty + u * RHO;
-        const uint64_t i = i0 + ri;
-        if (i >= n) break;
-        float a[DIM + 1];
+        for (int u = 0; u < R; ++u) {
+            const uint64_t i = i0 + ty + u * RHO;
+            if (i >= n) break;
+            f2 a2[DIM + 1];
 #pragma unroll
-        for (int k = 0; k <= DIM; ++k) a[k] = si[k][ri];
-#pragma unroll 1
-        for (int v = 0; v < R; ++v) {
-            const int cj = R == 1 ? tx : 2 * tx + 2 * RHO * (v >> 1) + (v & 1);
-            const uint64_t j = j0 + cj;
-            if (j >= i) continue;
-            float b[DIM + 1];
+            for (int k = 0; k <= DIM; ++k) a2[k] = si[k][ty + u * RHO];
 #pragma unroll
-            for (int k = 0; k <= DIM; ++k) b[k] = sj[k][cj];
-            if (hit_scalar<DIM>(a, b)) record(o, (uint32_t)i, (uint32_t)j);
+            for (int v = 0; v < RC; ++v) {
+                f2 s, q;
+                test(a2, v, s, q);
+                float s0, s1, q0, q1;
+                f2_unpack(s, s0, s1);
+                f2_unpack(q, q0, q1);
+                const uint64_t j = j0 + 2 * tx + 2 * RHO * v;
+                if (s0 <= q0 && j < i) record(o, (uint32_t)i, (uint32_t)j);
+                if (s1 <= q1 && j + 1 < i) record(o, (uint32_t)i, (uint32_t)(j + 1));
+            }
         }
     }
 }
 
+// 8 x 8 pairs per thread on 16 x 16 threads: registers capped at 64 so that
+// four blocks share an SM (uncapped the tile takes over 100 and three fit,
+// which leaves too few warps to cover the staging loads).
 template <int MAP, int RHO, int R, int DIM>
-__global__ void __launch_bounds__(RHO *RHO)
+__global__ void __launch_bounds__(RHO *RHO, (RHO == 16 && R == 8) ? 4 : 1)
     collide_kernel(const float *__restrict__ c, const float *__restrict__ rad, uint32_t n, CollideOut o, BlockMap bm)
 {
     uint32_t bi, bj;
@@ -219,7 +228,7 @@ extern "C" int tri_collide(const float *centres, const float *radii, uint32_t n,
 {
     if ((n && (!centres || !radii)) || !n_pairs || (!pairs && pair_cap > 0)) return TRI_EINVAL;
     if (dim < 1 || dim > 3 || !trihost::rho_ok(rho)) return TRI_EINVAL;
-    if (reg == 0) reg = 4;
+    if (reg == 0) reg = rho <= 16 ? 8 : 4;
     if ((reg != 1 && reg != 4 && reg != 8) || (reg == 8 && rho > 16)) return TRI_EINVAL;
     if (map < TRI_MAP_LAMBDA || map > TRI_MAP_LAMBDA_PDELTA) return TRI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;

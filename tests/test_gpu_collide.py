@@ -140,8 +140,8 @@ def test_collide_argument_errors():
 @pytest.mark.parametrize("dim", [1, 3])
 def test_collide_full_size(orc, dim):
     # the bench's workload: 65,536 spheres, about 4 contacts each, lambda with
-    # 16 x 16 threads of 4 x 4 pairs; every pair of the 2^31 tested
+    # 16 x 16 threads of 8 x 8 pairs (the default); every pair of the 2^31 tested
     n = 65536
     c, r = inputs.spheres(n, dim)
-    tot = _check(orc, c, r, map_id=tri().MAP_LAMBDA, rho=16, reg=4, cap=4 * n)
+    tot = _check(orc, c, r, map_id=tri().MAP_LAMBDA, rho=16, reg=0, cap=4 * n)
     assert 3.0 * n / 2 < tot < 4.5 * n / 2
