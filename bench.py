@@ -330,14 +330,30 @@ def run_suite(args):
         ws = torch.empty(max(tri.tet_at_workspace_size(n, 16, m) for m in (tri.MAP_LAMBDA, tri.MAP_BB)) // 8 + 1,
                          dtype=torch.float64, device=dev)
         t = {nm: graph_ms(lambda: tri.tet_at_energy(p, e, 1.0, m, 16, ws), 20)
-             for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB))}
+             for nm, m in (("lambda", tri.MAP_LAMBDA), ("lambda_table", tri.MAP_TET_TABLE), ("bb", tri.MAP_BB))}
         trip = n * (n - 1) * (n - 2) // 6
         tf = 40.0 * trip / (t["lambda"] * 1e-3) / 1e12
         emit({"row": "at_energy", "metric": "triplets/s", "unit": "triplets/s", "value": trip / (t["lambda"] * 1e-3),
+              "value_layer_table": trip / (t["lambda_table"] * 1e-3),
               "config": {"workload": "at_n1536_uniform_unit_density", "rho": 16}, "ms": t,
               "I_bb_over_lambda": t["bb"] / t["lambda"],
               "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
                            "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"}})
+
+    if want("at"):
+        # Section 6 / Section 7: the tetrahedral map alone (sentinel body), the
+        # closed-form cubic root against the table of layer starts and the m^3 box
+        n = 16384
+        o4 = torch.zeros(4, dtype=torch.int32, device=dev)
+        t = {nm: graph_ms(lambda: tri.tet_map_ex(m, n, 16, tri.BODY_SENTINEL, o4), 3)
+             for nm, m in (("lambda_cubic", tri.MAP_LAMBDA), ("lambda_table", tri.MAP_TET_TABLE),
+                           ("bb", tri.MAP_BB))}
+        mm = n // 16
+        emit({"row": "tet_map_only", "metric": "blocks/s", "unit": "blocks/s",
+              "value": mm * (mm + 1) * (mm + 2) // 6 / (t["lambda_table"] * 1e-3),
+              "config": {"workload": "sentinel body, n = 16384, rho = 16 (179,481,600 tetrahedral blocks)"},
+              "ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()},
+              "table_over_cubic": t["lambda_table"] / t["lambda_cubic"]})
 
     if want("collide"):
         # Section 5, test 3: collision detection of 65,536 spheres (smaller

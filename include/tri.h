@@ -66,8 +66,10 @@ typedef enum {
                                   launch per level; m must be a power of two */
     TRI_MAP_UTM = 4,           /* upper-triangular map of Avril et al., thread space
                                   (Section 4.2) */
-    TRI_MAP_LAMBDA_PDELTA = 5  /* lambda(omega) on the balanced m' x m' grid P_Delta,
+    TRI_MAP_LAMBDA_PDELTA = 5, /* lambda(omega) on the balanced m' x m' grid P_Delta,
                                   m' = ceil(sqrt(m(m+1)/2)) (Section 3.1) */
+    TRI_MAP_TET_TABLE = 6      /* tetrahedral calls only: lambda with the layer
+                                  found in a table of layer starts (Section 7) */
 } tri_map;
 
 /* Square-root estimate inside lambda (Section 4.1).  Every variant is followed
@@ -301,13 +303,30 @@ TRI_API int tri_collide(const float *centres, const float *radii, uint32_t n, ui
 TRI_API int tet_map(uint32_t n, uint32_t rho, int body, uint32_t *out, void *stream);
 
 /*
+ * tet_map_ex -- tet_map under a chosen map:
+ *   TRI_MAP_LAMBDA: as tet_map (the closed-form cubic root);
+ *   TRI_MAP_TET_TABLE: the succinct lookup table that Section 7 proposes: the
+ *     layer starts T_k for every T_k < 2^32 (2953 words, o(T_n), fixed at build
+ *     time in constant memory); a block finds its layer by binary search over
+ *     the first m entries (one broadcast read per step) and its (row, col) by
+ *     the 2-D lambda, so no cube root is taken;
+ *   TRI_MAP_BB: the m^3 bounding box of blocks, those outside the tetrahedron
+ *     leaving at once (Section 6 puts its waste at up to 6x).
+ *   Other arguments, results and errors as tet_map; TRI_EINVAL for other maps,
+ *   TRI_ERANGE for BB with m > 65535.
+ */
+TRI_API int tet_map_ex(int map, uint32_t n, uint32_t rho, int body, uint32_t *out, void *stream);
+
+/*
  * tet_at_energy -- Axilrod-Teller triple-dipole energy of n points, a
  * triplet-interaction n-body sum over the tetrahedral domain (Section 6):
  *   E = sum_{i>j>k} nu (1 + 3 cos g_i cos g_j cos g_k) / (r_ij r_jk r_ki)^3.
  *   xyz (device FP32 [n][3]); energy (device, one double).  Terms in FP32,
  *   block partials in FP64 written to the workspace, then summed in a fixed
  *   order by a second kernel, so the result is deterministic.
- *   map: TRI_MAP_LAMBDA (tetrahedral lambda) or TRI_MAP_BB (m^3 box with
+ *   map: TRI_MAP_LAMBDA (tetrahedral lambda), TRI_MAP_TET_TABLE (the same
+ *   blocks with the layer from the table of tet_map_ex; bit-identical
+ *   result) or TRI_MAP_BB (m^3 box with
  *   discard).  rho in {8,16,32}.
  *   Errors: TRI_EINVAL, TRI_ERANGE, TRI_ENOSPACE, TRI_ECUDA.
  */

@@ -5,6 +5,7 @@
 
 #include "f32x2.cuh"
 #include "tri_maps.cuh"
+#include "tet_table.cuh"
 
 using namespace tri;
 
@@ -22,10 +23,11 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
                           double *__restrict__ partial)
 {
     uint32_t L, R, C;
-    if constexpr (MAP == MAP_LAMBDA) {
+    if constexpr (MAP == MAP_LAMBDA || MAP == MAP_TET_TABLE) {
         const uint64_t w = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
         if (w >= nblocks) return;
-        tet_block((uint32_t)w, L, R, C);
+        if constexpr (MAP == MAP_TET_TABLE) tet_block_table((uint32_t)w, m, L, R, C);
+        else tet_block((uint32_t)w, L, R, C);
     } else {
         C = blockIdx.x;
         R = blockIdx.y;
@@ -125,7 +127,7 @@ __global__ void at_reduce_kernel(const double *__restrict__ partial, uint64_t co
 extern "C" int tet_at_workspace_size(uint32_t n, uint32_t rho, int map, size_t *bytes)
 {
     if (!bytes || !trihost::rho_ok(rho)) return TRI_EINVAL;
-    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_TET_TABLE && map != TRI_MAP_BB) return TRI_EINVAL;
     const uint64_t m = ((uint64_t)n + rho - 1) / rho;
     *bytes = (size_t)(T3(m) * sizeof(double));
     return TRI_OK;
@@ -139,9 +141,13 @@ static int at_energy_launch(const float *xyz, uint32_t n, double nu, double *ene
     const uint64_t m = ((uint64_t)n + rho - 1) / rho;
     const uint64_t nb = T3(m);
     const dim3 blk(rho, rho);
-    if (map == TRI_MAP_LAMBDA) {
+    if (map == TRI_MAP_LAMBDA || map == TRI_MAP_TET_TABLE) {
         if (nb > 0xFFFFFFFFull) return TRI_ERANGE;
-        at_kernel<MAP_LAMBDA><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, nb, partial);
+        if (map == TRI_MAP_LAMBDA)
+            at_kernel<MAP_LAMBDA><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, nb, partial);
+        else
+            at_kernel<MAP_TET_TABLE><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, nb,
+                                                                               partial);
     } else {
         if (m > 65535) return TRI_ERANGE;
         at_kernel<MAP_BB><<<dim3((unsigned)m, (unsigned)m, (unsigned)m), blk, 0, s>>>(xyz, n, nu, (uint32_t)m,
@@ -156,7 +162,7 @@ extern "C" int tet_at_energy(const float *xyz, uint32_t n, double nu, double *en
                              void *workspace, size_t ws_bytes, void *stream)
 {
     if (!xyz || !energy || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
-    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_TET_TABLE && map != TRI_MAP_BB) return TRI_EINVAL;
     size_t need = 0;
     tet_at_workspace_size(n, rho, map, &need);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 7)) return TRI_ENOSPACE;
@@ -207,7 +213,7 @@ extern "C" int tet_at_energy_noalloc(const float *xyz, uint32_t n, double nu, do
                                      void *stream)
 {
     if (!xyz || !energy || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
-    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_TET_TABLE && map != TRI_MAP_BB) return TRI_EINVAL;
     size_t need = 0;
     tet_at_workspace_size(n, rho, map, &need);
     if (need > sizeof(double) * AT_STATIC_PARTIALS) return TRI_ENOSPACE;  // more blocks than the array holds

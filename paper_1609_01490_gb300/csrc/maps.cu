@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "tri_maps.cuh"
+#include "tet_table.cuh"
 
 using namespace tri;
 
@@ -179,15 +180,25 @@ __global__ void lambda_verify_kernel(uint64_t w0, uint64_t w1, unsigned long lon
     }
 }
 
-// Tetrahedral blocks: block omega -> (L, R, C), L >= R >= C; thread (ty, tx)
+// Tetrahedral blocks: block omega -> (L, R, C), L >= R >= C, by the closed
+// form (MAP_LAMBDA) or the layer table (MAP_TET_TABLE), or the m^3 box
+// (MAP_BB, blocks outside the tetrahedron leave at once); thread (ty, tx)
 // takes i in block L, j in block R, and loops k over block C.
-template <int BODY>
-__global__ void tet_kernel(uint64_t nblocks, uint32_t n, uint32_t *out)
+template <int MAP, int BODY>
+__global__ void tet_kernel(uint64_t nblocks, uint32_t m, uint32_t n, uint32_t *out)
 {
-    const uint64_t w = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    if (w >= nblocks) return;
     uint32_t L, R, C;
-    tet_block((uint32_t)w, L, R, C);
+    if constexpr (MAP == MAP_BB) {
+        C = blockIdx.x;
+        R = blockIdx.y;
+        L = blockIdx.z;
+        if (R > L || C > R) return;
+    } else {
+        const uint64_t w = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        if (w >= nblocks) return;
+        if constexpr (MAP == MAP_TET_TABLE) tet_block_table((uint32_t)w, m, L, R, C);
+        else tet_block((uint32_t)w, L, R, C);
+    }
     const uint32_t rho = blockDim.x;
     const uint32_t i = L * rho + threadIdx.y, j = R * rho + threadIdx.x;
     if (i >= n || j >= i) return;
@@ -247,20 +258,37 @@ extern "C" int tri_lambda_verify(int sqrt_kind, int with_diag, uint64_t w_begin,
     return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
 
-extern "C" int tet_map(uint32_t n, uint32_t rho, int body, uint32_t *out, void *stream)
+extern "C" int tet_map_ex(int map, uint32_t n, uint32_t rho, int body, uint32_t *out, void *stream)
 {
     if (!out || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_TET_TABLE && map != TRI_MAP_BB) return TRI_EINVAL;
+    if (body != TRI_BODY_DUMMY && body != TRI_BODY_SENTINEL && body != TRI_BODY_COUNT) return TRI_EINVAL;
     if (n < 3) return TRI_OK;
     const uint64_t m = (n + rho - 1) / rho;
     const uint64_t nb = T3(m);
     if (nb > 0xFFFFFFFFull) return TRI_ERANGE;
+    if (map == TRI_MAP_BB && m > 65535) return TRI_ERANGE;
     cudaStream_t s = (cudaStream_t)stream;
-    const dim3 g = trihost::linear_grid(nb), blk(rho, rho);
-    switch (body) {
-    case TRI_BODY_DUMMY: tet_kernel<TRI_BODY_DUMMY><<<g, blk, 0, s>>>(nb, n, out); break;
-    case TRI_BODY_SENTINEL: tet_kernel<TRI_BODY_SENTINEL><<<g, blk, 0, s>>>(nb, n, out); break;
-    case TRI_BODY_COUNT: tet_kernel<TRI_BODY_COUNT><<<g, blk, 0, s>>>(nb, n, out); break;
-    default: return TRI_EINVAL;
+    const dim3 g = map == TRI_MAP_BB ? dim3((unsigned)m, (unsigned)m, (unsigned)m) : trihost::linear_grid(nb);
+    const dim3 blk(rho, rho);
+#define TRI_T(MP, BD) tet_kernel<MP, BD><<<g, blk, 0, s>>>(nb, (uint32_t)m, n, out)
+#define TRI_TB(MP)                                                                                             \
+    if (body == TRI_BODY_DUMMY) TRI_T(MP, TRI_BODY_DUMMY);                                                     \
+    else if (body == TRI_BODY_SENTINEL) TRI_T(MP, TRI_BODY_SENTINEL);                                          \
+    else TRI_T(MP, TRI_BODY_COUNT);
+    if (map == TRI_MAP_LAMBDA) {
+        TRI_TB(MAP_LAMBDA)
+    } else if (map == TRI_MAP_TET_TABLE) {
+        TRI_TB(MAP_TET_TABLE)
+    } else {
+        TRI_TB(MAP_BB)
     }
+#undef TRI_TB
+#undef TRI_T
     return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+extern "C" int tet_map(uint32_t n, uint32_t rho, int body, uint32_t *out, void *stream)
+{
+    return tet_map_ex(TRI_MAP_LAMBDA, n, rho, body, out, stream);
 }

@@ -105,6 +105,7 @@ enum : int {
     MAP_REC = TRI_MAP_REC,
     MAP_UTM = TRI_MAP_UTM,
     MAP_LAMBDA_PD = TRI_MAP_LAMBDA_PDELTA,
+    MAP_TET_TABLE = TRI_MAP_TET_TABLE,
     MAP_LAMBDA_ND = 100  // strict lambda (Eq. eq_theorem_nodiag), shifted by one row
 };
 

@@ -25,9 +25,9 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 # ------------------------------------------------------------- constants --
 TRI_OK, TRI_EINVAL, TRI_ERANGE, TRI_ECUDA, TRI_EOVERFLOW, TRI_ETIMEOUT, TRI_ENOSPACE = range(7)
-MAP_LAMBDA, MAP_BB, MAP_RB, MAP_REC, MAP_UTM, MAP_LAMBDA_PDELTA = range(6)
+MAP_LAMBDA, MAP_BB, MAP_RB, MAP_REC, MAP_UTM, MAP_LAMBDA_PDELTA, MAP_TET_TABLE = range(7)
 MAP_NAMES = {MAP_LAMBDA: "lambda", MAP_BB: "bb", MAP_RB: "rb", MAP_REC: "rec", MAP_UTM: "utm",
-             MAP_LAMBDA_PDELTA: "lambda_pdelta"}
+             MAP_LAMBDA_PDELTA: "lambda_pdelta", MAP_TET_TABLE: "tet_table"}
 SQRT_X, SQRT_R, SQRT_N = range(3)
 FP32, BF16X3, BF16X6 = range(3)
 BODY_DUMMY, BODY_SENTINEL, BODY_COUNT = range(3)
@@ -63,6 +63,7 @@ _SIGS = {
     "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
     "tri_collide": ([_vp, _vp, _u32, _u32, _i32, _u32, _u32, _vp, _vp, _u64, _vp, _vp], _i32),
     "tet_map": ([_u32, _u32, _i32, _vp, _vp], _i32),
+    "tet_map_ex": ([_i32, _u32, _u32, _i32, _vp, _vp], _i32),
     "tet_at_energy": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp, _sz, _vp], _i32),
     "tet_at_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
     "tet_at_energy_noalloc": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp], _i32),
@@ -141,6 +142,10 @@ def tri_lambda_verify(sqrt_kind: int, with_diag: bool, w_begin: int, w_end: int,
 
 def tet_map(n: int, rho: int, body: int, out, stream=None) -> None:
     _check("tet_map", _lib.tet_map(n, rho, body, _ptr(out), _stream(stream)))
+
+
+def tet_map_ex(map: int, n: int, rho: int, body: int, out, stream=None) -> None:
+    _check("tet_map_ex", _lib.tet_map_ex(map, n, rho, body, _ptr(out), _stream(stream)))
 
 
 # ------------------------------------------------------------------- EDM --

@@ -88,14 +88,21 @@ def test_dummy_and_sentinel_bodies_run():
     assert 0 <= int(out[0]) <= 2 * 4095
 
 
+@pytest.mark.parametrize("mapname", ["LAMBDA", "TET_TABLE", "BB"])
 @pytest.mark.parametrize("rho", [8, 16, 32])
-def test_tet_map_covers_strict_triplets(rho):
+def test_tet_map_covers_strict_triplets(rho, mapname):
+    # the closed-form cubic, the layer table (Section 7) and the m^3 box each
+    # cover every strict triplet exactly once
     import torch
     t = tri()
-    for n in (1, 2, 3, 4, 17, rho + 1, 100, 300):
+    map_id = getattr(t, "MAP_" + mapname)
+    for n in (1, 2, 3, 4, 17, rho + 1, 100, 300, 8 * rho + 5):
         size = math.comb(n, 3)
         out = torch.zeros(size + 64, dtype=torch.int32, device=dev())
-        t.tet_map(n, rho, t.BODY_COUNT, out)
+        if mapname == "LAMBDA":
+            t.tet_map(n, rho, t.BODY_COUNT, out)
+        else:
+            t.tet_map_ex(map_id, n, rho, t.BODY_COUNT, out)
         torch.cuda.synchronize()
         c = out.cpu().numpy()
         assert np.all(c[:size] == 1) and np.all(c[size:] == 0), (n, rho)
@@ -116,3 +123,16 @@ def test_tet_block_layers_match_oracle(orc):
     assert np.all(c == 1)
     L, R, C = orc.tet_enum(m)
     assert len(L) == m * (m + 1) * (m + 2) // 6
+
+
+def test_tet_map_ex_arguments():
+    import torch
+    t = tri()
+    out = torch.zeros(8, dtype=torch.int32, device=dev())
+    for args in ((t.MAP_RB, 100, 16, t.BODY_SENTINEL), (t.MAP_TET_TABLE, 100, 7, t.BODY_SENTINEL),
+                 (t.MAP_TET_TABLE, 100, 16, 9)):
+        with pytest.raises(t.TriError):
+            t.tet_map_ex(*args, out)
+    # 2952 layers of blocks is the last count below 2^32 blocks; one more is out of range
+    with pytest.raises(t.TriError):
+        t.tet_map_ex(t.MAP_TET_TABLE, 8 * 2953, 8, t.BODY_SENTINEL, out)

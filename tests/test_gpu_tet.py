@@ -48,3 +48,13 @@ def test_at_energy_c4_largest(orc):
     b = _energy(t, p, t.MAP_BB, 16)
     assert a == b                         # same partials, same order
     assert abs(a - ref) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("rho", [8, 16, 32])
+def test_at_energy_layer_table_is_bit_identical(rho):
+    # the layer table finds the same blocks as the cubic root, so every
+    # partial and the fixed-order sum are the same bits
+    t = tri()
+    for n in (3, 50, rho * 9 + 1, 700):
+        p = inputs.at_points(n, seed=77 + n)
+        assert _energy(t, p, t.MAP_TET_TABLE, rho) == _energy(t, p, t.MAP_LAMBDA, rho), (n, rho)
