@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -265,6 +266,33 @@ def run_suite(args):
               "ms": sweep, "I_bb_over_lambda_R": {n: v["bb"] / v["lambda_R"] for n, v in sweep.items()},
               "lambda_N_over_lambda_X": {n: v["lambda_N"] / v["lambda_X"] for n, v in sweep.items()},
               "lambda_R_over_lambda_X": {n: v["lambda_R"] / v["lambda_X"] for n, v in sweep.items()}})
+
+    if want("maps"):
+        # Section 4.1 / 4.2 taken as printed, without the exact integer step:
+        # the first omega (of all below 2^32) where each square-root estimate
+        # (with the paper's eps = 1e-4 for lambda_N and lambda_R) floors to the
+        # wrong row, and the first thread k where UTM's FP32 formula is wrong
+        fb = torch.empty(1, dtype=torch.int64, device=dev)
+
+        def first_error(map_id, sq, n_items, end):
+            fb.fill_(-1)
+            tri.tri_map_first_error(map_id, sq, n_items, 0, end, fb)
+            torch.cuda.synchronize()
+            v = int(fb.item()) & (2 ** 64 - 1)
+            return None if v == 2 ** 64 - 1 else v
+
+        lam = {}
+        for name, sq in (("lambda_X", tri.SQRT_X), ("lambda_R", tri.SQRT_R), ("lambda_N", tri.SQRT_N)):
+            w = first_error(tri.MAP_LAMBDA, sq, 0, 1 << 32)
+            row = None if w is None else int((math.isqrt(8 * w + 1) - 1) // 2)
+            lam[name] = {"first_bad_omega": w, "exact_rows_below": row}
+        utm = {}
+        for items in (1000, 2000, 3000, 4000, 6000, 8000, 16000, 32768):
+            utm[items] = first_error(tri.MAP_UTM, tri.SQRT_X, items, items * (items - 1) // 2)
+        emit({"row": "printed_formula_exactness", "metric": "first failing index", "unit": "index",
+              "config": {"workload": "every omega < 2^32 (lambda); every thread of n items (UTM)"},
+              "lambda": lam, "utm_first_bad_k": utm,
+              "note": "exact_rows_below rows of blocks map correctly: n <= rows x rho elements"})
 
     if want("edm"):
         # a5: the paper-size EDM, N = 2048, d = 3, rho = 16 (8.4 MB output, L2-resident)

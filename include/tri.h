@@ -134,6 +134,26 @@ TRI_API int tri_lambda_verify(int sqrt_kind, int with_diag, uint64_t w_begin, ui
                       unsigned long long *result, void *stream);
 
 /*
+ * tri_map_first_error -- where the printed formulas, taken without the exact
+ * integer correction this library applies, first give a wrong result:
+ *   map = TRI_MAP_LAMBDA: for every omega in [begin, end) (end <= 2^32), the
+ *     row floor(e + eps - 1/2), e the FP32 estimate sqrt_kind of
+ *     sqrt(2 omega + 1/4), eps = 1e-4 for TRI_SQRT_N and TRI_SQRT_R and 0 for
+ *     TRI_SQRT_X (Section 4.1), against the exact row (n_items unused);
+ *   map = TRI_MAP_UTM: for every thread k in [begin, end) of n_items items
+ *     (2 <= n_items <= 2^31, end <= n_items (n_items - 1) / 2), the pair (a, b)
+ *     of the formula of Section 4.2 with its square root argument and a in
+ *     FP32, against the exact pair (sqrt_kind unused but checked).
+ *   first_bad (device uint64, set by the caller, e.g. to UINT64_MAX): lowered
+ *   atomically to the smallest failing omega or k in the range.
+ *   Errors: TRI_EINVAL (null first_bad, begin > end, bad map or sqrt_kind),
+ *   TRI_ERANGE (range limits above, or more than 2^31 - 1 blocks of 256
+ *   threads in one call), TRI_ECUDA.
+ */
+TRI_API int tri_map_first_error(int map, int sqrt_kind, uint64_t n_items, uint64_t begin, uint64_t end,
+                                unsigned long long *first_bad, void *stream);
+
+/*
  * tri_edm -- Euclidean distance matrix over i >= j (Section 5, test 2):
  *   out[i(i+1)/2 + j] = sqrt(sum_k (x[i][k] - x[j][k])^2), the diagonal 0.
  *   x (device, FP32) row-major [n][d]; out (device, FP32) n(n+1)/2 entries.

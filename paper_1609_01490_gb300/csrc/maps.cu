@@ -216,7 +216,85 @@ __global__ void tet_kernel(uint64_t nblocks, uint32_t m, uint32_t n, uint32_t *o
     }
 }
 
+// ------------------------------------------------ the printed formulas ----
+// Section 4.1 as printed: the row of omega is the FP32 estimate of
+// sqrt(2 omega + 1/4) - 1/2 (plus eps = 1e-4 for lambda_N and lambda_R),
+// floored, with no integer correction.
+template <int SQ>
+__device__ __forceinline__ uint32_t lambda_row_printed(uint32_t w)
+{
+    const float eps = SQ == TRI_SQRT_X ? 0.0f : 1e-4f;
+    const float est = sqrt_estimate<SQ>(fmaf(2.0f, (float)w, 0.25f)) + eps - 0.5f;
+    return __float2uint_rz(est);
+}
+
+// Section 4.2 as printed (Avril et al.): thread k of n items,
+// a = floor((-(2n + 1) + sqrt(4n^2 - 4n - 8k + 1)) / -2), b = (a + 1) + k -
+// (a - 1)(2n - a)/2, with the square root's argument and a in FP32.
+__device__ __forceinline__ void utm_pair_printed(uint64_t k, uint64_t n, uint64_t &a, uint64_t &b)
+{
+    const float fn = (float)n, fk = (float)k;
+    const float disc = 4.0f * fn * fn - 4.0f * fn - 8.0f * fk + 1.0f;
+    const float af = floorf((-(2.0f * fn + 1.0f) + sqrtf(disc)) / -2.0f);
+    const long long ai = af < 0.0f ? 0 : (long long)af;
+    a = (uint64_t)ai;
+    b = (uint64_t)((long long)a + 1 + (long long)k - ((long long)a - 1) * (2 * (long long)n - (long long)a) / 2);
+}
+
+// Lowers *first_bad to the smallest index in [i0, i1) where the printed
+// formula disagrees with the exact map (one index per thread).
+template <int MAPK, int SQ>
+__global__ void first_error_kernel(uint64_t n_items, uint64_t i0, uint64_t i1, unsigned long long *first_bad)
+{
+    const uint64_t x = i0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (x < i1) {
+        if constexpr (MAPK == MAP_UTM) {
+            uint32_t ea, eb;
+            utm_pair(x, n_items, ea, eb);
+            uint64_t a, b;
+            utm_pair_printed(x, n_items, a, b);
+            bad = a != ea || b != eb;
+        } else {
+            uint32_t ei, ej;
+            lambda_diag<TRI_SQRT_R>((uint32_t)x, ei, ej);
+            bad = lambda_row_printed<SQ>((uint32_t)x) != ei;
+        }
+    }
+    const unsigned any = __ballot_sync(0xffffffffu, bad);
+    if (any && (threadIdx.x & 31) == (unsigned)(__ffs(any) - 1)) atomicMin(first_bad, (unsigned long long)x);
+}
+
 }  // namespace
+
+extern "C" int tri_map_first_error(int map, int sqrt_kind, uint64_t n_items, uint64_t begin, uint64_t end,
+                                   unsigned long long *first_bad, void *stream)
+{
+    if (!first_bad || begin > end) return TRI_EINVAL;
+    if (sqrt_kind < TRI_SQRT_X || sqrt_kind > TRI_SQRT_N) return TRI_EINVAL;
+    if (map == TRI_MAP_LAMBDA) {
+        if (end > (1ull << 32)) return TRI_ERANGE;
+    } else if (map == TRI_MAP_UTM) {
+        if (n_items < 2 || n_items > (1ull << 31) || end > n_items * (n_items - 1) / 2) return TRI_ERANGE;
+    } else {
+        return TRI_EINVAL;
+    }
+    if (begin == end) return TRI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned tpb = 256;
+    const dim3 g = trihost::linear_grid((end - begin + tpb - 1) / tpb);
+    if (g.y > 1) return TRI_ERANGE;  // one launch covers at most 2^31 - 1 blocks of 256
+    if (map == TRI_MAP_UTM) {
+        first_error_kernel<MAP_UTM, TRI_SQRT_X><<<g, tpb, 0, s>>>(n_items, begin, end, first_bad);
+    } else if (sqrt_kind == TRI_SQRT_X) {
+        first_error_kernel<MAP_LAMBDA, TRI_SQRT_X><<<g, tpb, 0, s>>>(n_items, begin, end, first_bad);
+    } else if (sqrt_kind == TRI_SQRT_R) {
+        first_error_kernel<MAP_LAMBDA, TRI_SQRT_R><<<g, tpb, 0, s>>>(n_items, begin, end, first_bad);
+    } else {
+        first_error_kernel<MAP_LAMBDA, TRI_SQRT_N><<<g, tpb, 0, s>>>(n_items, begin, end, first_bad);
+    }
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
 
 extern "C" int tri_map_launch(int map, int sqrt_kind, uint32_t n, uint32_t rho, int with_diag, int body,
                               uint32_t *out, void *stream)

@@ -52,6 +52,7 @@ _SIGS = {
     "tri_version": ([], _i32),
     "tri_map_launch": ([_i32, _i32, _u32, _u32, _i32, _i32, _vp, _vp], _i32),
     "tri_lambda_verify": ([_i32, _i32, _u64, _u64, _vp, _vp], _i32),
+    "tri_map_first_error": ([_i32, _i32, _u64, _u64, _u64, _vp, _vp], _i32),
     "tri_edm": ([_vp, _u32, _u32, _vp, _i32, _u32, _u32, _i32, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
     "tri_edm_prepare": ([_vp, _u32, _u32, _i32, _vp, _sz, _vp], _i32),
@@ -133,6 +134,12 @@ def tri_map_launch(map: int, sqrt_kind: int, n: int, rho: int, with_diag: bool, 
                    stream=None) -> None:
     _check("tri_map_launch", _lib.tri_map_launch(map, sqrt_kind, n, rho, 1 if with_diag else 0, body,
                                                  _ptr(out), _stream(stream)))
+
+
+def tri_map_first_error(map: int, sqrt_kind: int, n_items: int, begin: int, end: int, first_bad,
+                        stream=None) -> None:
+    _check("tri_map_first_error", _lib.tri_map_first_error(map, sqrt_kind, n_items, begin, end, _ptr(first_bad),
+                                                           _stream(stream)))
 
 
 def tri_lambda_verify(sqrt_kind: int, with_diag: bool, w_begin: int, w_end: int, result, stream=None) -> None:

@@ -136,3 +136,53 @@ def test_tet_map_ex_arguments():
     # 2952 layers of blocks is the last count below 2^32 blocks; one more is out of range
     with pytest.raises(t.TriError):
         t.tet_map_ex(t.MAP_TET_TABLE, 8 * 2953, 8, t.BODY_SENTINEL, out)
+
+
+def _first_error(t, map_id, sq, n_items, begin, end):
+    import torch
+    fb = torch.full((1,), -1, dtype=torch.int64, device=dev())  # all ones: no failure seen
+    t.tri_map_first_error(map_id, sq, n_items, begin, end, fb)
+    torch.cuda.synchronize()
+    v = int(fb.item()) & (2 ** 64 - 1)
+    return None if v == 2 ** 64 - 1 else v
+
+
+def _exact_rows(w):
+    r = ((np.sqrt(8.0 * w.astype(np.float64) + 1.0) - 1.0) // 2).astype(np.int64)
+    r -= (r * (r + 1) // 2 > w)
+    r += ((r + 1) * (r + 2) // 2 <= w)
+    return r
+
+
+def test_printed_lambda_x_first_error_matches_cpu():
+    # Section 4.1's lambda_X taken as printed (FP32 sqrtf, no correction): the
+    # GPU's first wrong omega below 2^32 is the first one a step-by-step FP32
+    # emulation on the host finds (2 w is exact, the sum and the root round
+    # once each, as fmaf and sqrtf do)
+    t = tri()
+    fx = _first_error(t, t.MAP_LAMBDA, t.SQRT_X, 0, 0, 1 << 32)
+    assert fx is not None and fx < 200_000_000
+    first = None
+    for a in range(0, fx + 1, 1 << 24):
+        w = np.arange(a, min(fx + 1, a + (1 << 24)), dtype=np.int64)
+        x = np.float32(2.0) * w.astype(np.float32) + np.float32(0.25)
+        row = np.floor(np.sqrt(x) - np.float32(0.5)).astype(np.int64)
+        bad = np.nonzero(row != _exact_rows(w))[0]
+        if len(bad):
+            first = int(w[bad[0]])
+            break
+    assert first == fx
+
+
+def test_printed_formulas_first_errors_run():
+    # the eps variants and UTM as printed: every range call succeeds; UTM is
+    # exact for 1000 items (its discriminant stays below 2^24)
+    t = tri()
+    for sq in (t.SQRT_R, t.SQRT_N):
+        f = _first_error(t, t.MAP_LAMBDA, sq, 0, 0, 1 << 32)
+        assert f is None or 0 < f < (1 << 32)
+    assert _first_error(t, t.MAP_UTM, t.SQRT_X, 1000, 0, 1000 * 999 // 2) is None
+    with pytest.raises(t.TriError):
+        _first_error(t, t.MAP_UTM, t.SQRT_X, 1000, 0, 1000 * 999 // 2 + 1)
+    with pytest.raises(t.TriError):
+        _first_error(t, t.MAP_BB, t.SQRT_X, 0, 0, 10)
