@@ -134,6 +134,18 @@ TRI_API int tri_lambda_verify(int sqrt_kind, int with_diag, uint64_t w_begin, ui
                       unsigned long long *result, void *stream);
 
 /*
+ * tri_peak_probe -- arithmetic peak probe for the ALU rooflines (not in the
+ * paper): `blocks` blocks of 256 threads, each thread running 8 independent
+ * chains of `iters` fused multiply-adds: kind 0 FP32 (fma.rn.f32), 1 FP32 in
+ * two-lane form (fma.rn.f32x2, two results per instruction), 2 FP64.  The
+ * caller times the launch on its stream; *flop (host) receives the floating-
+ * point operations launched (2 per result).  sink (device FP32, blocks x 256)
+ * receives one value per thread so that the chains are kept.
+ *   Errors: TRI_EINVAL, TRI_ECUDA.
+ */
+TRI_API int tri_peak_probe(int kind, uint32_t blocks, uint32_t iters, float *sink, double *flop, void *stream);
+
+/*
  * tri_map_first_error -- where the printed formulas, taken without the exact
  * integer correction this library applies, first give a wrong result:
  *   map = TRI_MAP_LAMBDA: for every omega in [begin, end) (end <= 2^32), the

@@ -53,6 +53,7 @@ _SIGS = {
     "tri_map_launch": ([_i32, _i32, _u32, _u32, _i32, _i32, _vp, _vp], _i32),
     "tri_lambda_verify": ([_i32, _i32, _u64, _u64, _vp, _vp], _i32),
     "tri_map_first_error": ([_i32, _i32, _u64, _u64, _u64, _vp, _vp], _i32),
+    "tri_peak_probe": ([_i32, _u32, _u32, _vp, _vp, _vp], _i32),
     "tri_edm": ([_vp, _u32, _u32, _vp, _i32, _u32, _u32, _i32, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
     "tri_edm_prepare": ([_vp, _u32, _u32, _i32, _vp, _sz, _vp], _i32),
@@ -134,6 +135,14 @@ def tri_map_launch(map: int, sqrt_kind: int, n: int, rho: int, with_diag: bool, 
                    stream=None) -> None:
     _check("tri_map_launch", _lib.tri_map_launch(map, sqrt_kind, n, rho, 1 if with_diag else 0, body,
                                                  _ptr(out), _stream(stream)))
+
+
+def tri_peak_probe(kind: int, blocks: int, iters: int, sink, stream=None) -> float:
+    """Launches the FMA probe; returns the flop it performs (the caller times it)."""
+    flop = ctypes.c_double(0.0)
+    _check("tri_peak_probe", _lib.tri_peak_probe(kind, blocks, iters, _ptr(sink), ctypes.addressof(flop),
+                                                 _stream(stream)))
+    return flop.value
 
 
 def tri_map_first_error(map: int, sqrt_kind: int, n_items: int, begin: int, end: int, first_bad,
