@@ -245,6 +245,21 @@ def run_suite(args):
         d.setdefault("peaks", {"source": peak_src})
         print(json.dumps(d), flush=True)
 
+    use_cpu = not args.no_cpu
+    if use_cpu:
+        import oracle
+        oracle.lib()
+        cores = oracle.threads()
+
+    def cpu_leg(fn, units, unit, sample):
+        """The oracle on a bounded sample of the row's workload, on the host cores."""
+        if not use_cpu:
+            return None
+        t0 = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t0
+        return {"value": units / dt, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
+
     peaks_alu = measure_alu_peaks()
     fp32_derived = fp32_peak
     fp32_peak = peaks_alu["fp32"]
@@ -267,7 +282,9 @@ def run_suite(args):
         emit({"row": "map_only", "metric": "mapped elements/s", "unit": "elements/s",
               "config": {"workload": "sentinel body (map cost only)", "n": n, "rho": 16},
               "ms": times, "value": {k: elems / (v * 1e-3) for k, v in times.items()},
-              "I_bb_over": {k: times["bb"] / v for k, v in times.items()}})
+              "I_bb_over": {k: times["bb"] / v for k, v in times.items()},
+          "cpu_baseline": cpu_leg(lambda: oracle.lambda_enum(16384), 16384 * 16385 // 2, "elements/s",
+                                  "enumeration matrix walk, m = 16384 rows")})
 
     if want("maps"):
         # the square-root strategies of Section 4.1 over n (the map-only sweep
@@ -316,7 +333,8 @@ def run_suite(args):
 
     if want("edm"):
         # a5: the paper-size EDM, N = 2048, d = 3, rho = 16 (8.4 MB output, L2-resident)
-        x = torch.from_numpy(inputs.edm_uniform_points(2048, 3, seed=1609)).to(dev)
+        xh = inputs.edm_uniform_points(2048, 3, seed=1609)
+        x = torch.from_numpy(xh).to(dev)
         o = torch.empty(2048 * 2049 // 2, dtype=torch.float32, device=dev)
         t = {nm: graph_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=1), 200)
              for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB),
@@ -327,12 +345,15 @@ def run_suite(args):
               "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
               "roofline": {"bound": "hbm", "achieved": 4.0 * P / (t["lambda"] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                            "frac": 4.0 * P / (t["lambda"] * 1e-3) / 1e9 / hbm,
-                           "note": "8.4 MB output stays in L2 across back-to-back launches"}})
+                           "note": "8.4 MB output stays in L2 across back-to-back launches"},
+              "cpu_baseline": cpu_leg(lambda: [oracle.edm_rows(xh) for _ in range(50)], 50 * P, "pairs/s",
+                                      "the whole triangle 50 times, FP64")})
 
     if want("edm"):
         # a2/a5 at scale: N = 65536, d = 3 (store-bound, 8.6 GB of output) with the
         # paper's block shape (one pair per thread, rho = 16) and with 4 x 4 pairs per thread
-        x = torch.from_numpy(inputs.edm_uniform_points(65536, 3, seed=1609)).to(dev)
+        xh = inputs.edm_uniform_points(65536, 3, seed=1609)
+        x = torch.from_numpy(xh).to(dev)
         o = torch.empty(65536 * 65537 // 2, dtype=torch.float32, device=dev)
         P = 65536 * 65537 // 2
         for reg in (1, 4):
@@ -344,14 +365,18 @@ def run_suite(args):
                   "value": P / (t["lambda"] * 1e-3),
                   "config": {"workload": "edm_n65536_d3_uniform", "rho": 16, "reg": reg,
                              "pairs_per_thread": reg * reg}, "ms": t, "I_bb_over_lambda": t["bb"] / t["lambda"],
-                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}})
+                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm},
+                  "cpu_baseline": cpu_leg(lambda: oracle.edm_rows(xh, 63488, 65536),
+                                          65536 * 65537 // 2 - 63488 * 63489 // 2, "pairs/s",
+                                          "rows 63488 .. 65535 (the last 2048 rows), FP64")})
         del x, o
         torch.cuda.empty_cache()
 
     if want("life"):
         # a6: triangular Life, n = 16384, 100 steps, rho = 16
         n = 16384
-        a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)
+        gh = inputs.ca_grid(n, seed=1609)
+        a = torch.from_numpy(gh).to(dev)
         b = torch.zeros_like(a)
 
         def life(m):
@@ -368,12 +393,14 @@ def run_suite(args):
               "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 16}, "ms_per_step": t,
               "I_bb_over_lambda": t["bb"] / t["lambda"],
               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                           "algorithmic_bytes_per_step": 2 * cells}})
+                           "algorithmic_bytes_per_step": 2 * cells},
+              "cpu_baseline": cpu_leg(lambda: oracle.ca_step(gh), cells, "cells/s", "one step of the n = 16384 grid")})
 
     if want("at"):
         # a7: Axilrod-Teller energy over the tetrahedral domain, N = 1536, rho = 16
         n = 1536
-        p = torch.from_numpy(inputs.at_points(n, seed=1610)).to(dev)
+        ph = inputs.at_points(n, seed=1610)
+        p = torch.from_numpy(ph).to(dev)
         e = torch.zeros(1, dtype=torch.float64, device=dev)
         ws = torch.empty(max(tri.tet_at_workspace_size(n, 16, m) for m in (tri.MAP_LAMBDA, tri.MAP_BB)) // 8 + 1,
                          dtype=torch.float64, device=dev)
@@ -386,7 +413,9 @@ def run_suite(args):
               "config": {"workload": "at_n1536_uniform_unit_density", "rho": 16}, "ms": t,
               "I_bb_over_lambda": t["bb"] / t["lambda"],
               "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
-                           "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"}})
+                           "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"},
+              "cpu_baseline": cpu_leg(lambda: oracle.at_energy(ph[:1000]), 1000 * 999 * 998 // 6, "triplets/s",
+                                      "the first 1000 points (1.66e8 triplets), FP64")})
 
     if want("at"):
         # Section 6 / Section 7: the tetrahedral map alone (sentinel body), the
@@ -401,7 +430,9 @@ def run_suite(args):
               "value": mm * (mm + 1) * (mm + 2) // 6 / (t["lambda_table"] * 1e-3),
               "config": {"workload": "sentinel body, n = 16384, rho = 16 (179,481,600 tetrahedral blocks)"},
               "ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()},
-              "table_over_cubic": t["lambda_table"] / t["lambda_cubic"]})
+              "table_over_cubic": t["lambda_table"] / t["lambda_cubic"],
+              "cpu_baseline": cpu_leg(lambda: oracle.tet_enum(800), 800 * 801 * 802 // 6, "blocks/s",
+                                      "tetrahedral enumeration, m = 800 layers")})
 
     if want("collide"):
         # Section 5, test 3: collision detection of 65,536 spheres (smaller
@@ -418,6 +449,9 @@ def run_suite(args):
             cs, rs = inputs.spheres(n, dim)
             cd, rd = torch.from_numpy(cs).to(dev), torch.from_numpy(rs).to(dev)
             ops = 4 if dim == 1 else 10  # FP32 sub, mul, add per pair (no fused multiply-add)
+            r0 = max(0, n - 8192)
+            cpu_base = cpu_leg(lambda: oracle.collide_pairs(cs, rs, r0, n), n * (n - 1) // 2 - r0 * (r0 - 1) // 2,
+                               "pairs/s", f"rows {r0} .. {n - 1} (every pair j < i), FP32 test")
             for reg in (1, 4, 8):
                 maps = [("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB), ("rec", tri.MAP_REC)]
                 if reg == 1:
@@ -432,7 +466,8 @@ def run_suite(args):
                       "I_bb_over_lambda": t["bb"] / t["lambda"],
                       "roofline": {"bound": "alu", "achieved": top, "peak": alu_peak, "unit": "TOP/s",
                                    "frac": top / alu_peak,
-                                   "note": f"{ops} FP32 operations per pair; peak: measured FFMA results/s"}})
+                                   "note": f"{ops} FP32 operations per pair; peak: measured FFMA results/s"},
+                      "cpu_baseline": cpu_base})
             del cd, rd
         del npairs, cnt, plist
 
@@ -466,7 +501,10 @@ def run_suite(args):
         emit({"row": "edm_batched", "metric": "pairs/s", "unit": "pairs/s", "value": total / (best * 1e-3),
               "config": {"workload": "1000 instances, N log-uniform [64, 8192], d = 64", "pairs": total}, "ms": tb,
               "speedup_over_separate": tb["separate_1000_launches"] / best,
-              "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak}})
+              "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak},
+              "cpu_baseline": cpu_leg(lambda: [oracle.edm_rows(xc[int(pt_off[k]): int(pt_off[k]) + int(sizes[k])])
+                                               for k in range(20)], int(tri_len[:20].sum()), "pairs/s",
+                                      "the first 20 instances, FP64")})
 
 
     # -------------------------------------------------------------- our arm -----
