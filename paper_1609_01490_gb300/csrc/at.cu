@@ -34,16 +34,32 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
         L = blockIdx.z;
         if (R > L || C > R) return;
     }
-    // block C's points by coordinate, so that two consecutive k load as one 8-byte word
-    __shared__ __align__(8) float pkx[32], pky[32], pkz[32];
+    // The block's pair quantities, once each: b(j, k) = |p_j - p_k|^2 for j in
+    // block R and c(i, k) = |p_k - p_i|^2 for i in block L, k in block C, with
+    // the same operations as the per-triplet form (so the same bits); rows
+    // padded by two floats so that a warp's 8-byte loads of (k, k + 1) fall on
+    // distinct banks.
+    __shared__ __align__(8) float sb[32][34], sc[32][34];
     __shared__ double wsum[32];
     const uint32_t rho = blockDim.x;
     const uint32_t tid = threadIdx.y * rho + threadIdx.x;
-    if (tid < rho) {
-        const uint32_t k = C * rho + tid;
-        pkx[tid] = k < n ? p[3 * k + 0] : 0.0f;
-        pky[tid] = k < n ? p[3 * k + 1] : 0.0f;
-        pkz[tid] = k < n ? p[3 * k + 2] : 0.0f;
+    {
+        const uint32_t kk = C * rho + threadIdx.x;
+        const uint32_t jj = R * rho + threadIdx.y, ii = L * rho + threadIdx.y;
+        float bv = 0.0f, cv = 0.0f;
+        if (kk < n) {
+            const float xk = p[3 * kk], yk = p[3 * kk + 1], zk = p[3 * kk + 2];
+            if (jj < n) {
+                const float ex = p[3 * jj] - xk, ey = p[3 * jj + 1] - yk, ez = p[3 * jj + 2] - zk;
+                bv = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            }
+            if (ii < n) {
+                const float fx = xk - p[3 * ii], fy = yk - p[3 * ii + 1], fz = zk - p[3 * ii + 2];
+                cv = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+            }
+        }
+        sb[threadIdx.y][threadIdx.x] = bv;
+        sc[threadIdx.y][threadIdx.x] = cv;
     }
     __syncthreads();
     const uint32_t i = L * rho + threadIdx.y, j = R * rho + threadIdx.x;
@@ -54,18 +70,12 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
         const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
         const float a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const uint32_t kend = min(j, (C + 1) * rho) - C * rho;  // k < j
-        const f2 XJ = f2_pack(xj, xj), YJ = f2_pack(yj, yj), ZJ = f2_pack(zj, zj);
-        const f2 XI = f2_pack(xi, xi), YI = f2_pack(yi, yi), ZI = f2_pack(zi, zi);
+        const float *brow = sb[threadIdx.x], *crow = sc[threadIdx.y];
         const f2 A = f2_pack(a, a), K = f2_pack(0.375f, 0.375f), ONE = f2_pack(1.0f, 1.0f);
         f2 S = f2_pack(0.0f, 0.0f);
         uint32_t t = 0;
         for (; t + 1 < kend; t += 2) {
-            const f2 PX = *reinterpret_cast<const f2 *>(&pkx[t]), PY = *reinterpret_cast<const f2 *>(&pky[t]),
-                     PZ = *reinterpret_cast<const f2 *>(&pkz[t]);
-            const f2 ex = f2_sub(XJ, PX), ey = f2_sub(YJ, PY), ez = f2_sub(ZJ, PZ);
-            const f2 fx = f2_sub(PX, XI), fy = f2_sub(PY, YI), fz = f2_sub(PZ, ZI);
-            const f2 b = f2_fma(ex, ex, f2_fma(ey, ey, f2_mul(ez, ez)));
-            const f2 c = f2_fma(fx, fx, f2_fma(fy, fy, f2_mul(fz, fz)));
+            const f2 b = *reinterpret_cast<const f2 *>(&brow[t]), c = *reinterpret_cast<const f2 *>(&crow[t]);
             const f2 q = f2_mul(f2_mul(A, b), c);
             const f2 P = f2_mul(f2_mul(f2_sub(f2_add(A, c), b), f2_sub(f2_add(A, b), c)), f2_sub(f2_add(b, c), A));
             float q0, q1;
@@ -78,10 +88,7 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
         f2_unpack(S, s0, s1);
         s = s0 + s1;
         for (; t < kend; ++t) {
-            const float ex = xj - pkx[t], ey = yj - pky[t], ez = zj - pkz[t];
-            const float fx = pkx[t] - xi, fy = pky[t] - yi, fz = pkz[t] - zi;
-            const float b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            const float c = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+            const float b = brow[t], c = crow[t];
             const float q = a * b * c;
             const float P = (a + c - b) * (a + b - c) * (b + c - a);
             const float rs = rsqrtf(q);
