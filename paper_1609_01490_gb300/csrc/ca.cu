@@ -102,10 +102,108 @@ __global__ void __launch_bounds__(4 * RHO) ca_kernel(const uint8_t *__restrict__
     }
 }
 
+// Conway's rule bit-sliced: one bit per cell, 32 cells per word.  Tile S x S,
+// S = 4*RHO, with S/2 threads: thread t takes the 32-cell strip c = t % NS
+// (NS = S/32) of the tile rows [HR g, HR g + HR), g = t / NS, HR = S/16, and
+// reads its HR + 2 input rows (one above, one below) as two 16-byte loads
+// each.  Each row's 32 bytes become one word (bit b = byte b non-zero,
+// cleared past the diagonal and outside rows [0, n)); the cells left and
+// right of the strip come from the neighbouring lanes' words by shuffle, or,
+// at the tile's edges, from a 4-byte load beyond it.  Per row, the three
+// horizontal neighbours give a parity word s and a majority word c (the count
+// of the three is s + 2c); over three rows the 3 x 3 sum is
+// ones + 2 (k + x + 2y) with ones, k the parity and majority of the three s,
+// and x, y those of the three c.  The cell lives on iff the sum (itself
+// included) is 3, or 4 with the cell alive.
+__device__ __forceinline__ uint32_t alive_nibble(uint32_t w)  // bit b: byte b of w non-zero
+{
+    const uint32_t h = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;  // bit 7 of each non-zero byte
+    return (h * 0x00204081u) >> 28;  // bits 7, 15, 23, 31 -> 28, 29, 30, 31
+}
+
+__device__ __forceinline__ uint32_t nibble_bytes(uint32_t nib)  // bit b -> byte b (0 or 1)
+{
+    return (nib * 0x00204081u) & 0x01010101u;
+}
+
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (a & c) | (b & c); }
+
+template <int MAP, int RHO>
+__global__ void __launch_bounds__(2 * RHO) ca_life_bits_kernel(const uint8_t *__restrict__ in,
+                                                               uint8_t *__restrict__ out, uint32_t n, size_t ld,
+                                                               BlockMap bm)
+{
+    constexpr int S = 4 * RHO, NT = S / 2, NS = S / 32, HR = S / 16;
+    constexpr unsigned FULL = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
+    uint32_t bi, bj;
+    if (!map_block<MAP>(bm, bi, bj)) return;
+    const int t = threadIdx.x, c = t % NS, g = t / NS;
+    const long long cc = (long long)bj * S + 32 * c;      // first cell (byte) column of the strip
+    const long long a0 = (long long)bi * S + HR * g - 1;  // global row of the first register row
+    uint32_t B[HR + 2], sH[HR + 2], cH[HR + 2];
+#pragma unroll
+    for (int q = 0; q < HR + 2; ++q) {
+        const long long a = a0 + q;
+        const bool rok = a >= 0 && a < (long long)n;
+        const uint8_t *row = in + (rok ? (size_t)a * ld : 0);
+        uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
+        if (rok && cc <= a) v0 = __ldg(reinterpret_cast<const uint4 *>(row + cc));
+        if (rok && cc + 16 <= a) v1 = __ldg(reinterpret_cast<const uint4 *>(row + cc + 16));
+        uint32_t b = alive_nibble(v0.x) | (alive_nibble(v0.y) << 4) | (alive_nibble(v0.z) << 8) |
+                     (alive_nibble(v0.w) << 12) | (alive_nibble(v1.x) << 16) | (alive_nibble(v1.y) << 20) |
+                     (alive_nibble(v1.z) << 24) | (alive_nibble(v1.w) << 28);
+        const long long inside = a - cc;  // columns cc .. cc + inside lie in the domain
+        b = !rok || inside < 0 ? 0u : (inside >= 31 ? b : b & ((2u << inside) - 1u));
+        B[q] = b;
+        // the cells beyond the strip's ends
+        uint32_t lb = 0u, rb = 0u;
+        if (c == 0 && rok && cc >= 4 && cc - 1 <= a)
+            lb = __ldg(reinterpret_cast<const uint32_t *>(row + cc - 4)) >> 24 ? 1u : 0u;
+        if (c == NS - 1 && rok && cc + 32 <= a)
+            rb = __ldg(reinterpret_cast<const uint32_t *>(row + cc + 32)) & 0xFFu ? 1u : 0u;
+        const uint32_t up = __shfl_up_sync(FULL, b, 1, NS);    // strip c - 1
+        const uint32_t dn = __shfl_down_sync(FULL, b, 1, NS);  // strip c + 1
+        if (c > 0) lb = up >> 31;
+        if (c < NS - 1) rb = dn & 1u;
+        const uint32_t L = (b << 1) | lb, R = (b >> 1) | (rb << 31);  // left and right neighbour of each cell
+        sH[q] = L ^ b ^ R;
+        cH[q] = maj3(L, b, R);
+    }
+#pragma unroll
+    for (int q = 1; q <= HR; ++q) {
+        const long long a = a0 + q;
+        if (a >= (long long)n) break;
+        if (cc > a) continue;  // the strip is past the diagonal in this row
+        const uint32_t ones = sH[q - 1] ^ sH[q] ^ sH[q + 1], k = maj3(sH[q - 1], sH[q], sH[q + 1]);
+        const uint32_t x = cH[q - 1] ^ cH[q] ^ cH[q + 1], y = maj3(cH[q - 1], cH[q], cH[q + 1]);
+        const uint32_t three = ones & (x ^ k) & ~y;                             // sum 3
+        const uint32_t four = ~ones & ((y & ~x & ~k) | (~y & x & k));           // sum 4
+        const uint32_t nx = three | (four & B[q]);
+        uint8_t *dst = out + (size_t)a * ld + cc;
+        const uint4 o0 = make_uint4(nibble_bytes(nx & 0xFu), nibble_bytes((nx >> 4) & 0xFu),
+                                    nibble_bytes((nx >> 8) & 0xFu), nibble_bytes((nx >> 12) & 0xFu));
+        const uint4 o1 = make_uint4(nibble_bytes((nx >> 16) & 0xFu), nibble_bytes((nx >> 20) & 0xFu),
+                                    nibble_bytes((nx >> 24) & 0xFu), nibble_bytes(nx >> 28));
+        if (cc + 31 <= a) {
+            *reinterpret_cast<uint4 *>(dst) = o0;
+            *reinterpret_cast<uint4 *>(dst + 16) = o1;
+        } else {
+            for (int b = 0; cc + b <= a; ++b) dst[b] = (uint8_t)((nx >> b) & 1u);
+        }
+    }
+}
+
 template <int MAP, bool LIFE>
 void launch_rule(uint32_t rho, dim3 g, cudaStream_t s, const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
                  uint32_t table, BlockMap bm)
 {
+    if constexpr (LIFE) {
+        switch (rho) {
+        case 8: ca_life_bits_kernel<MAP, 8><<<g, 16, 0, s>>>(in, out, n, ld, bm); return;
+        case 16: ca_life_bits_kernel<MAP, 16><<<g, 32, 0, s>>>(in, out, n, ld, bm); return;
+        default: ca_life_bits_kernel<MAP, 32><<<g, 64, 0, s>>>(in, out, n, ld, bm); return;
+        }
+    }
     switch (rho) {
     case 8: ca_kernel<MAP, 8, LIFE><<<g, 32, 0, s>>>(in, out, n, ld, table, bm); break;
     case 16: ca_kernel<MAP, 16, LIFE><<<g, 64, 0, s>>>(in, out, n, ld, table, bm); break;
