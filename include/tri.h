@@ -282,8 +282,10 @@ TRI_API int tri_edm_batched_workspace_size(uint32_t count, size_t *bytes);
  *   in, out (device uint8, 16-byte aligned) row-major with leading dimension
  *   ld (bytes); ld >= n and ld a multiple of 16; in != out (no aliasing).
  *   map: LAMBDA, LAMBDA_PDELTA, BB, RB or REC.  rho in {8,16,32}: each block
- *   covers a (4 rho) x (4 rho) cell tile with 4 rho threads, each thread a
- *   16-cell strip of rho/4 consecutive rows (one 16-byte load per row).
+ *   covers a (4 rho) x (4 rho) cell tile.  Conway's rule runs bit-sliced with
+ *   2 rho threads, each a 32-cell strip of rho/4 consecutive rows held as one
+ *   bit per cell (two 16-byte loads per row); other rules run with 4 rho
+ *   threads, each a 16-cell strip of byte counters (one 16-byte load per row).
  *   Errors: TRI_EINVAL (null, aliasing, bad ld/rho/map), TRI_ERANGE, TRI_ECUDA.
  */
 TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
