@@ -379,18 +379,21 @@ def run_suite(args):
         a = torch.from_numpy(gh).to(dev)
         b = torch.zeros_like(a)
 
-        def life(m):
+        def life(m, rho):
             def run():
                 for s in range(100):
                     src, dst = (a, b) if s % 2 == 0 else (b, a)
-                    tri.tri_ca_step(src, dst, n, map=m, rho=16)
+                    tri.tri_ca_step(src, dst, n, map=m, rho=rho)
             return run
-        t = {nm: graph_ms(life(m), 1) / 100 for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB),
-                                                          ("rb", tri.MAP_RB), ("rec", tri.MAP_REC))}
+        # 128 x 128 cell tiles (rho = 32) are the fastest; rho = 16 beside them
+        t = {nm: graph_ms(life(m, 32), 1) / 100 for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB),
+                                                              ("rb", tri.MAP_RB), ("rec", tri.MAP_REC))}
+        t16 = {nm: graph_ms(life(m, 16), 1) / 100 for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB))}
         cells = n * (n + 1) // 2
         gbs = 2.0 * cells / (t["lambda"] * 1e-3) / 1e9
         emit({"row": "life_step", "metric": "cell updates/s", "unit": "cells/s", "value": cells / (t["lambda"] * 1e-3),
-              "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 16}, "ms_per_step": t,
+              "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 32}, "ms_per_step": t,
+              "ms_per_step_rho16": t16,
               "I_bb_over_lambda": t["bb"] / t["lambda"],
               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                            "algorithmic_bytes_per_step": 2 * cells},
@@ -402,15 +405,18 @@ def run_suite(args):
         ph = inputs.at_points(n, seed=1610)
         p = torch.from_numpy(ph).to(dev)
         e = torch.zeros(1, dtype=torch.float64, device=dev)
-        ws = torch.empty(max(tri.tet_at_workspace_size(n, 16, m) for m in (tri.MAP_LAMBDA, tri.MAP_BB)) // 8 + 1,
+        ws = torch.empty(max(tri.tet_at_workspace_size(n, r, tri.MAP_BB) for r in (16, 32)) // 8 + 1,
                          dtype=torch.float64, device=dev)
-        t = {nm: graph_ms(lambda: tri.tet_at_energy(p, e, 1.0, m, 16, ws), 20)
+        # 32 x 32 threads with 32 values of k each are the fastest; rho = 16 beside them
+        t = {nm: graph_ms(lambda: tri.tet_at_energy(p, e, 1.0, m, 32, ws), 20)
              for nm, m in (("lambda", tri.MAP_LAMBDA), ("lambda_table", tri.MAP_TET_TABLE), ("bb", tri.MAP_BB))}
+        t16 = {nm: graph_ms(lambda: tri.tet_at_energy(p, e, 1.0, m, 16, ws), 20)
+               for nm, m in (("lambda", tri.MAP_LAMBDA), ("lambda_table", tri.MAP_TET_TABLE), ("bb", tri.MAP_BB))}
         trip = n * (n - 1) * (n - 2) // 6
         tf = 40.0 * trip / (t["lambda"] * 1e-3) / 1e12
         emit({"row": "at_energy", "metric": "triplets/s", "unit": "triplets/s", "value": trip / (t["lambda"] * 1e-3),
               "value_layer_table": trip / (t["lambda_table"] * 1e-3),
-              "config": {"workload": "at_n1536_uniform_unit_density", "rho": 16}, "ms": t,
+              "config": {"workload": "at_n1536_uniform_unit_density", "rho": 32}, "ms": t, "ms_rho16": t16,
               "I_bb_over_lambda": t["bb"] / t["lambda"],
               "roofline": {"bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
                            "note": "about 40 FP32 flop per triplet (plus one MUFU rsqrt)"},
