@@ -66,3 +66,32 @@ def test_host_side_argument_errors(lib):
     assert L.tri_ca_step(ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), 64, 60, 8, 12, 0, 16, None) == 1  # ld
     L.tri_status_string.restype = ctypes.c_char_p
     assert b"TRI_ERANGE" in L.tri_status_string(2)
+
+
+def test_host_side_argument_errors_of_the_later_calls(lib):
+    # every one of these is rejected on the host before any CUDA call
+    import ctypes
+    L = ctypes.CDLL(lib)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    dummy = vp(4096)
+    L.tri_collide.argtypes = [vp, vp, u32, u32, i32, u32, u32, vp, vp, u64, vp, vp]
+    assert L.tri_collide(dummy, dummy, 100, 3, 0, 16, 0, None, None, 0, None, None) == 1     # no n_pairs
+    assert L.tri_collide(dummy, dummy, 100, 4, 0, 16, 0, None, None, 0, dummy, None) == 1    # dim 4
+    assert L.tri_collide(dummy, dummy, 100, 3, 0, 16, 2, None, None, 0, dummy, None) == 1    # reg 2
+    assert L.tri_collide(dummy, dummy, 100, 3, 0, 32, 8, None, None, 0, dummy, None) == 1    # 8 x 8 at rho 32
+    assert L.tri_collide(dummy, dummy, 100, 3, 6, 16, 0, None, None, 0, dummy, None) == 1    # tetrahedral map
+    assert L.tri_collide(dummy, dummy, 100, 3, 0, 16, 0, None, None, 5, dummy, None) == 1    # cap, no list
+    L.tet_map_ex.argtypes = [i32, u32, u32, i32, vp, vp]
+    assert L.tet_map_ex(2, 100, 16, 1, dummy, None) == 1     # RB is not a tetrahedral map
+    assert L.tet_map_ex(6, 100, 12, 1, dummy, None) == 1     # rho 12
+    assert L.tet_map_ex(6, 8 * 2953, 8, 1, dummy, None) == 2  # 2953 layers exceed 2^32 blocks
+    L.tri_map_first_error.argtypes = [i32, i32, u64, u64, u64, vp, vp]
+    assert L.tri_map_first_error(0, 0, 0, 0, 10, None, None) == 1          # no result word
+    assert L.tri_map_first_error(0, 0, 0, 0, (1 << 32) + 1, dummy, None) == 2
+    assert L.tri_map_first_error(4, 0, 1000, 0, 1000 * 999 // 2 + 1, dummy, None) == 2
+    assert L.tri_map_first_error(1, 0, 0, 0, 10, dummy, None) == 1          # BB has no printed formula
+    L.tri_peak_probe.argtypes = [i32, u32, u32, vp, vp, vp]
+    assert L.tri_peak_probe(3, 1, 1, dummy, dummy, None) == 1
+    L.tet_at_workspace_size.argtypes = [u32, u32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    n = ctypes.c_size_t(0)
+    assert L.tet_at_workspace_size(96, 16, 6, ctypes.byref(n)) == 0 and n.value == 8 * (6 * 7 * 8 // 6)
