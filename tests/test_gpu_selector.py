@@ -32,10 +32,11 @@ def test_autotune_small_live(tmp_path, monkeypatch):
 
 
 def test_selector_on_held_out_groups():
-    # On the committed GB300 sweep most candidates of a configuration lie within
-    # a few percent of each other, and (lambda, rho = 16) is a strong default:
-    # the model's picks are on par with it (within 2 points of regret) and
-    # far from a random candidate's.
+    # On the committed GB300 sweep the fixed default (lambda, rho = 16) is up to
+    # a third slower than the best candidate for the Life step and the AT
+    # energy (where rho = 32 wins) and close to it for the EDM; the model's
+    # picks are at least as good as the default on the held-out configurations
+    # and far from a random candidate's.
     dev()
     from paper_1609_01490_gb300 import selector
     table = json.load(open(TABLE))
@@ -45,7 +46,7 @@ def test_selector_on_held_out_groups():
     model, loss = selector.train(X, y, steps=3000)
     assert loss < 0.05  # relative log-time fit: a few percent
     res = selector.evaluate(model, table, held)
-    assert res["regret_model"] <= res["regret_default"] + 0.02
+    assert res["regret_model"] <= res["regret_default"]
     assert res["regret_model"] < 0.1 * res["regret_random"]
     # a pick costs a fraction of the exhaustive sweep's timed kernel work alone
     assert res["pick_seconds"] * 1e3 < 0.1 * res["exhaustive_timed_ms_per_group"]
@@ -58,7 +59,7 @@ def test_selector_leave_one_out():
     table = json.load(open(TABLE))
     res = selector.evaluate_loo(table, steps=1500)
     assert res["loo_groups"] == len(table["groups"])
-    assert res["loo_regret_model"] <= res["loo_regret_default"] + 0.02
+    assert res["loo_regret_model"] <= res["loo_regret_default"]
     assert res["loo_model_better_or_equal"] >= res["loo_groups"] // 2
 
 
