@@ -144,3 +144,16 @@ def test_invariants_on_general_fp32():
     np.testing.assert_array_equal(np.concatenate([a_j, b_j]), pj)
     idx = np.array([0, 1, 299, 300, n - 1])
     np.testing.assert_array_equal(oracle.collide_count_of(c, r, idx), cnt[idx])
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_sphere_workload_contact_rate(dim):
+    # the workload recipe: radii U[0, a) with (n - 1) E[V_dim(r_i + r_j)] = kappa
+    # gives about kappa contacts per sphere (fewer near the box walls)
+    from paper_1609_01490_gb300 import inputs
+    n, kappa = 20000, 4.0
+    c, r = inputs.spheres(n, dim, kappa=kappa, seed=11)
+    assert c.shape == (n, dim) and c.dtype == np.float32 and r.dtype == np.float32
+    assert float(r.min()) >= 0.0 and float(r.max()) < inputs.sphere_radius_max(n, dim, kappa)
+    cnt, _, _ = oracle.collide_counts(c, r)
+    assert 0.85 * kappa < cnt.mean() <= 1.02 * kappa
