@@ -129,11 +129,9 @@ def test_invariants_on_general_fp32():
     assert cnt.sum() == 2 * len(pi) and len(pi) > 50
     # the test is symmetric in i and j: relabelling the spheres relabels the pairs
     perm = rng.permutation(n)
-    inv = np.argsort(perm)
     _, qi, qj = oracle.collide_counts(c[perm], r[perm])
     mapped = {(max(int(perm[a]), int(perm[b])), min(int(perm[a]), int(perm[b]))) for a, b in zip(qi, qj)}
     assert mapped == pairs
-    del inv
     # scaling centres and radii by 2 scales every FP32 step exactly
     _, si, sj = oracle.collide_counts(c * np.float32(2), r * np.float32(2))
     assert set(zip(si.tolist(), sj.tolist())) == pairs
