@@ -231,6 +231,12 @@ extern "C" int tri_collide(const float *centres, const float *radii, uint32_t n,
     if (reg == 0) reg = rho <= 16 ? 8 : 4;
     if ((reg != 1 && reg != 4 && reg != 8) || (reg == 8 && rho > 16)) return TRI_EINVAL;
     if (map < TRI_MAP_LAMBDA || map > TRI_MAP_LAMBDA_PDELTA) return TRI_EINVAL;
+    if (n > 0) {  // every range check before the first call that touches the device
+        const int st = map == TRI_MAP_UTM
+                           ? ((uint64_t)n + 1) * n / 2 <= 0xFFFFFFFFull ? TRI_OK : TRI_ERANGE
+                           : trihost::map_range(map, ((uint64_t)n + rho * reg - 1) / (rho * reg));
+        if (st != TRI_OK) return st;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(n_pairs, 0, sizeof(*n_pairs), s) != cudaSuccess) return TRI_ECUDA;
     if (count && n && cudaMemsetAsync(count, 0, sizeof(uint32_t) * n, s) != cudaSuccess) return TRI_ECUDA;

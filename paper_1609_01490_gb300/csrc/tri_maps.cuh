@@ -245,6 +245,25 @@ inline uint64_t isqrt_ceil(uint64_t v)
     return r * r == v ? r : r + 1;
 }
 
+// Whether a 2-D block map can cover m block rows with CUDA's grid limits:
+// TRI_OK, TRI_ERANGE (too many blocks; REC with m not a power of two) or
+// TRI_EINVAL (not a 2-D block map).  m is taken in 64 bits so that a block
+// count computed from n near 2^32 cannot wrap.
+inline int map_range(int map, uint64_t m)
+{
+    switch (map) {
+    case TRI_MAP_LAMBDA: return m <= 0xFFFFFFFFull && tri::T2(m) <= 0xFFFFFFFFull ? TRI_OK : TRI_ERANGE;
+    case TRI_MAP_LAMBDA_PDELTA:
+        return m <= 0xFFFFFFFFull && tri::T2(m) <= 0xFFFFFFFFull && isqrt_ceil(tri::T2(m)) <= 65535 ? TRI_OK
+                                                                                                    : TRI_ERANGE;
+    case TRI_MAP_BB: return m <= 65535 ? TRI_OK : TRI_ERANGE;
+    case TRI_MAP_RB: return ((m & 1u) ? (m + 1) / 2 : m / 2 + 1) <= 65535 && m <= 65535 * 2 ? TRI_OK : TRI_ERANGE;
+    case TRI_MAP_REC:
+        return m <= 0xFFFFFFFFull && is_pow2((uint32_t)m) && (m < 2 || m / 2 <= 65535) ? TRI_OK : TRI_ERANGE;
+    default: return TRI_EINVAL;
+    }
+}
+
 // The launches of a 2-D block map over m block rows: go(tag, grid, bm) is
 // called once per launch (REC: once per level) with tag an
 // std::integral_constant holding the kernel's MAP; returns a tri_status.

@@ -81,6 +81,12 @@ def test_host_side_argument_errors_of_the_later_calls(lib):
     assert L.tri_collide(dummy, dummy, 100, 3, 0, 32, 8, None, None, 0, dummy, None) == 1    # 8 x 8 at rho 32
     assert L.tri_collide(dummy, dummy, 100, 3, 6, 16, 0, None, None, 0, dummy, None) == 1    # tetrahedral map
     assert L.tri_collide(dummy, dummy, 100, 3, 0, 16, 0, None, None, 5, dummy, None) == 1    # cap, no list
+    # block counts beyond the map's range are refused before the device is touched, also
+    # where n + tile - 1 would wrap around 2^32
+    assert L.tri_collide(dummy, dummy, 0xFFFFFFF0, 3, 0, 16, 0, None, None, 0, dummy, None) == 2  # lambda
+    assert L.tri_collide(dummy, dummy, 65535 * 128 + 1, 3, 1, 16, 0, None, None, 0, dummy, None) == 2  # BB
+    assert L.tri_collide(dummy, dummy, 100000, 3, 4, 16, 0, None, None, 0, dummy, None) == 2  # UTM threads
+    assert L.tri_collide(dummy, dummy, 300, 3, 3, 16, 0, None, None, 0, dummy, None) == 2    # REC, 3 rows
     L.tet_map_ex.argtypes = [i32, u32, u32, i32, vp, vp]
     assert L.tet_map_ex(2, 100, 16, 1, dummy, None) == 1     # RB is not a tetrahedral map
     assert L.tet_map_ex(6, 100, 12, 1, dummy, None) == 1     # rho 12
