@@ -76,9 +76,11 @@ def test_ca_c1_size_one_step(orc):
     t = tri()
     n = 16384
     g = inputs.ca_grid(n, seed=1609)
-    for m in (t.MAP_LAMBDA, t.MAP_BB):
-        got = _run(t, g, n, 1, m, 16)
-        assert np.array_equal(got, orc.ca_step(g)), m
+    ref = orc.ca_step(g)
+    # rho = 32 is the tile the bench's Life row times; rho = 16 beside it
+    for m, rho in ((t.MAP_LAMBDA, 32), (t.MAP_BB, 32), (t.MAP_RB, 32), (t.MAP_LAMBDA, 16), (t.MAP_BB, 16)):
+        got = _run(t, g, n, 1, m, rho)
+        assert np.array_equal(got, ref), (m, rho)
 
 
 def test_ca_hundred_steps(orc):

@@ -48,6 +48,10 @@ def test_at_energy_c4_largest(orc):
     b = _energy(t, p, t.MAP_BB, 16)
     assert a == b                         # same partials, same order
     assert abs(a - ref) <= 1e-5 * scale
+    # rho = 32, the tile the bench's AT row times: layer table, cubic root and box agree bit for bit
+    c = _energy(t, p, t.MAP_TET_TABLE, 32)
+    assert c == _energy(t, p, t.MAP_LAMBDA, 32) == _energy(t, p, t.MAP_BB, 32)
+    assert abs(c - ref) <= 1e-5 * scale
 
 
 @pytest.mark.parametrize("rho", [8, 16, 32])
