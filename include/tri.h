@@ -179,7 +179,9 @@ TRI_API int tri_map_first_error(int map, int sqrt_kind, uint64_t n_items, uint64
  *   TRI_MAP_LAMBDA or TRI_MAP_BB; rho and reg are ignored;
  *   needs `workspace` of tri_edm_workspace_size bytes (256-byte aligned).
  *   Pairs whose Gram estimate of d^2 falls below tau*(|x_i|^2 + |x_j|^2) are
- *   recomputed in FP64 by direct differences; n_flagged (device uint64,
+ *   recomputed in FP64 by direct differences (BF16X6: tau = (2 + 24 c)
+ *   2^-23 / 1.96e-5 for c = ceil(d / 64) K chunks, which bounds every other
+ *   distance's relative error by 1e-5; BF16X3: tau = 0.0625, no bound); n_flagged (device uint64,
  *   may be NULL) receives how many were flagged.  If more were flagged than
  *   the workspace list holds, the recompute pass scans the whole triangle
  *   instead (slower, same result).
@@ -211,8 +213,12 @@ TRI_API int tri_edm_workspace_size(uint32_t n, uint32_t d, int prec, size_t *byt
  *     map: TRI_MAP_LAMBDA (2 x 2 blocks of tiles in lambda order) or
  *     TRI_MAP_BB.  Runs as clusters of two CTAs (tcgen05 cta_group::2).  A
  *     device wait that exceeds 2 s sets the workspace status word (int at
- *     byte 8) to TRI_ETIMEOUT and the kernel returns; if the two CTAs of a
- *     pair cannot share their tensor-memory address the word becomes
+ *     byte 8) to TRI_ETIMEOUT; both CTAs of the pair then stop, wait for
+ *     their copies and MMAs in flight, free their tensor memory and return.
+ *     The workspace's uint64 at byte 40 (cleared by tri_edm_prepare) sets a
+ *     shorter limit, in ns, for the waits between the kernel's roles; it
+ *     exists so that tests can make those waits run out.  If the two CTAs of
+ *     a pair cannot share their tensor-memory address the word becomes
  *     TRI_ECUDA and the pair does no work.
  *   tri_edm_fixup: recomputes the flagged pairs in FP64 by direct differences
  *     (or, when the list overflowed, every pair whose stored distance passes a
@@ -243,10 +249,44 @@ TRI_API int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out, in
  * completes after the last copy, so synchronise it before reading out_host.
  * out_host and out_dev hold the same triangle as tri_edm's out.
  * Errors: TRI_EINVAL (null pointer, zero size, bad map or prec, unaligned
- * out_dev), TRI_ERANGE / TRI_ENOSPACE as tri_edm, TRI_ECUDA.
+ * out_dev), TRI_ERANGE / TRI_ENOSPACE as tri_edm, TRI_ECUDA.  After an error
+ * in a later band, `stream` still completes only after the copies already
+ * queued, so the buffers may be reused once the stream is synchronised.
  */
 TRI_API int tri_edm_host(const float *x_host, uint32_t n, uint32_t d, float *out_host, int map, int prec,
                          uint32_t bands, float *x_dev, float *out_dev, void *workspace, size_t ws_bytes,
+                         unsigned long long *n_flagged, void *stream);
+
+/*
+ * One EDM split across processes, one per GPU (the row order of Section 3's
+ * enumeration matrix makes each band of rows one contiguous range of the
+ * packed output, so the ranks compute without exchanging anything).
+ *
+ *   tri_edm_partition: host only, no device work.  The rows [*row_begin,
+ *     *row_end) and the packed entries [*pair_begin, *pair_end) =
+ *     [T(row_begin), T(row_end)), T(i) = i(i+1)/2, that rank `rank` of
+ *     `ranks` computes: bands of whole 256-row unit rows (the tensor-core
+ *     kernel's unit of work), the band of rank r starting at the first unit
+ *     row whose packed offset reaches r/ranks of the n(n+1)/2 pairs.  The
+ *     bands are disjoint and cover the triangle in rank order; a rank may
+ *     get an empty band when n is small.  Errors: TRI_EINVAL (null pointer,
+ *     ranks = 0, rank >= ranks), TRI_ERANGE (n > 92681).
+ *   tri_edm_rows: the tensor-core EDM (prec TRI_BF16X3 or TRI_BF16X6, map
+ *     TRI_MAP_LAMBDA or TRI_MAP_BB) of the rows [row_begin, row_end) only,
+ *     with row_begin a multiple of 256 and row_end a multiple of 256 or n:
+ *     x (device) holds all n points (every row pairs with all columns j <= i);
+ *     out_band (device, 16-byte aligned, T(row_end) - T(row_begin) floats)
+ *     receives the packed entries T(row_begin) .. T(row_end) - 1 from its
+ *     first element on, the same values as tri_edm writes there.  Runs
+ *     tri_edm_prepare, the Gram kernel over the band's units and the FP64
+ *     recompute of the band's flagged pairs; workspace and n_flagged as
+ *     tri_edm.  Errors as tri_edm; TRI_EINVAL also for a band not on unit
+ *     rows.
+ */
+TRI_API int tri_edm_partition(uint32_t n, uint32_t ranks, uint32_t rank, uint32_t *row_begin, uint32_t *row_end,
+                              uint64_t *pair_begin, uint64_t *pair_end);
+TRI_API int tri_edm_rows(const float *x, uint32_t n, uint32_t d, uint32_t row_begin, uint32_t row_end,
+                         float *out_band, int map, int prec, void *workspace, size_t ws_bytes,
                          unsigned long long *n_flagged, void *stream);
 
 /*

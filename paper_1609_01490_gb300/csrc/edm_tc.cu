@@ -57,6 +57,8 @@ constexpr int NORM_FLOATS = 2 * 32;       // per epilogue warp: norms of its 32 
 constexpr int STG_ROWS = 8;                // rows staged at a time by a row group
 constexpr int STG_LD = TILE + 4;           // staging row: 128 distances shifted by the row's 16-byte phase
 constexpr int STG_FLOATS = STG_ROWS * STG_LD;  // one staging buffer
+// shared floats per row group: two staging buffers (P = 2 stages its stores)
+__host__ __device__ constexpr int group_floats(int P) { return P == 2 ? 2 * STG_FLOATS : 0; }
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 constexpr int TQ = 8;                      // unit queue slots (producer -> MMA and epilogues, both CTAs)
 constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last unit
@@ -65,8 +67,23 @@ constexpr uint32_t DYN_CHUNK = 2;          // units per grab from the global cou
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int MAX_STAGES = 12;             // B ring depth cap (16 KB stages)
 
-constexpr float TAU_X6 = 0.3125f;  // flag threshold for hi/mid/lo (derived bound)
 constexpr float TAU_X3 = 0.0625f;  // flag threshold for hi/lo (empirical)
+
+// Flag threshold for hi/mid/lo with nkc 64-wide K chunks.  The Gram term's
+// error is at most 2^-23 (dropped products) plus 2^-23 per FP32 accumulation
+// step (24 MMAs of K = 16 per chunk: 6 plane products x 4) of
+// sum_k |x_ik x_jk| <= (|x_i|^2 + |x_j|^2) / 2; with the norms' and the final
+// combination's roundings, |error of d^2| <= (2 + 24 nkc) 2^-23 (|x_i|^2 +
+// |x_j|^2).  The relative error of d is about half that of d^2, and the
+// square root adds up to ~1.5e-7, so a pair with d^2 > tau (|x_i|^2 + |x_j|^2)
+// stays within 1e-5 when tau = (2 + 24 nkc) 2^-23 / (2 (1e-5 - 2e-7)).
+// tau = 0.158 (d <= 64), 0.304 (d <= 128), 0.450 (d <= 192).
+float tau_x6(uint32_t nkc) { return (float)((2.0 + 24.0 * nkc) * std::ldexp(1.0, -23) / (2.0 * (1e-5 - 2e-7))); }
+
+float flag_tau(int prec, uint32_t d)
+{
+    return prec == TRI_BF16X6 ? tau_x6((d + KCH - 1) / KCH) : TAU_X3;
+}
 
 struct WsLayout {
     size_t hdr, norms, planes, flags, total;
@@ -74,8 +91,10 @@ struct WsLayout {
 };
 
 // Workspace: [header 256 B: flag counter (u64 at 0), status (int at 8), tile
-// counter (u64 at 16)][norms n FP32][planes
-// P x n x dp BF16][flag list cap x u64], each part 256-byte aligned.
+// counter (u64 at 16), tri_edm_host's two list-start slots (u64 at 24, 32),
+// the wait limit of the Gram kernel's waits between roles in ns (u64 at 40,
+// 0: WAIT_LIMIT_NS)][norms n FP32][planes P x n x dp BF16][flag list cap x
+// u64], each part 256-byte aligned.  tri_edm_prepare clears the header.
 WsLayout ws_layout(uint32_t n, uint32_t d, int prec)
 {
     const int P = prec == TRI_BF16X6 ? 3 : 2;
@@ -147,7 +166,8 @@ __device__ __forceinline__ uint64_t global_ns()
 // abort_flag is null: the drain waits at exit must not cut short a copy or
 // MMA that is still writing).
 template <bool CL = false>
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns = WAIT_LIMIT_NS)
 {
     auto test = [&]() { return CL ? mbar_try_cl(bar, parity) : mbar_try(bar, parity); };
     if (test()) return true;
@@ -156,7 +176,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         if (test()) return true;
         if ((it & 15) == 0) {
             if (abort_flag && *abort_flag) return false;
-            if (global_ns() - start > WAIT_LIMIT_NS) return false;
+            if (global_ns() - start > limit_ns) return false;
             __nanosleep(64);
         }
     }
@@ -165,10 +185,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // mbar_wait by lane 0 with the result broadcast, so the whole warp leaves
 // together and agrees on it.
 template <bool CL = false>
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint64_t limit_ns)
 {
     int r = 0;
-    if ((threadIdx.x & 31) == 0) r = mbar_wait<CL>(bar, parity, abort_flag) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) r = mbar_wait<CL>(bar, parity, abort_flag, limit_ns) ? 1 : 0;
     return __shfl_sync(0xffffffffu, r, 0) != 0;
 }
 
@@ -216,6 +236,17 @@ __device__ __forceinline__ void mbar_arrive_cl_release(uint32_t cl_bar)
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Cancels bytes that a phase was told to expect (copies that never started).
+__device__ __forceinline__ void mbar_complete_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void st_cl_u32(uint32_t cl_addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cl_addr), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void st_cl_u64(uint32_t cl_addr, unsigned long long v)
@@ -380,6 +411,7 @@ struct GramArgs {
     unsigned long long *flag_count, *flag_list, flag_cap;
     unsigned long long *tile_counter;  // zero at launch
     int *status;
+    const unsigned long long *wait_limit;  // ns a wait between roles may take; 0: WAIT_LIMIT_NS
 };
 
 // Unit number u -> (R, C): lambda over the triangle of units (Eq. eq_gmap),
@@ -411,6 +443,24 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// The same barrier with a vote: true iff `ok` holds in every thread of the
+// group.  A named barrier cannot give up, so the row group takes a unit (and
+// the barriers inside it) only when all four of its warps have one; after a
+// failed wait in any of them, all four stop together.
+__device__ __forceinline__ bool named_sync_all(uint32_t id, uint32_t count, bool ok)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 // 1/sqrt by the MUFU unit (flush-to-zero approximation; relative error a few
 // 2^-23, far inside the 1e-5 the distances are held to).
 __device__ __forceinline__ float rsqrt_approx(float x)
@@ -440,7 +490,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;  // this CTA's row block
     constexpr uint32_t stage_bytes = CHUNK_BYTES;               // one plane of one K chunk
-    constexpr uint32_t stg_floats = P == 2 ? (NEPI / 4) * 2 * STG_FLOATS : 0;  // two staging buffers per row group
+    constexpr uint32_t stg_floats = (NEPI / 4) * group_floats(P);  // store staging of the row groups
     const uint32_t sA = base;                                   // [kc][p] chunks
     const uint32_t sB = base + a_bytes;                         // [stage] chunks of one plane
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
@@ -457,6 +507,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // producer into both CTAs
     __shared__ volatile unsigned long long s_tq[TQ];
     __shared__ __align__(8) uint64_t s_tqbar[2 * TQ];
+    // the odd CTA's copy counts (B stages, A row blocks), reported to the even
+    // CTA's producer at the end so that it can wait for every copy in flight
+    __shared__ uint32_t s_odd_loads[2];
+    __shared__ __align__(8) uint64_t s_odd_done;
     const uint32_t b_tqfull = smem_u32(s_tqbar), b_tqempty = b_tqfull + 8 * TQ;
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -486,6 +540,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             mbar_init(b_tqfull + 8 * s, 1);
             mbar_init(b_tqempty + 8 * s, 2 + 2 * NEPI);
         }
+        mbar_init(smem_u32(&s_odd_done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -504,6 +559,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // run only if the two allocations agree.
     const bool run = ld_cl_u32(mapa(smem_u32(&s_tmem), other)) == tmem;
     if (!run && threadIdx.x == 0) atomicExch(g.status, (int)TRI_ECUDA);
+    // limit of the waits between roles (the waits that drain copies and MMAs
+    // before exit always keep WAIT_LIMIT_NS)
+    const uint64_t wl = *g.wait_limit ? (uint64_t)*g.wait_limit : WAIT_LIMIT_NS;
 
     // cluster addresses of the even CTA's shared barriers and of the other CTA's queue
     const uint32_t L_fullA = mapa(b_fullA, 0), L_fullB = mapa(b_fullB, 0), L_tempty = mapa(b_tempty, 0);
@@ -521,7 +579,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // Pushed by the even CTA's producer into both CTAs.
     auto tq_push = [&](uint32_t k, unsigned long long v) {
         const uint32_t slot = k % TQ;
-        if (!mbar_wait(b_tqempty + 8 * slot, ((k / TQ) & 1) ^ 1, &s_abort)) return false;
+        if (!mbar_wait(b_tqempty + 8 * slot, ((k / TQ) & 1) ^ 1, &s_abort, wl)) return false;
         s_tq[slot] = v;
         mbar_arrive(b_tqfull + 8 * slot);
         st_cl_u64(O_tq + 8 * slot, v);
@@ -531,7 +589,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // by one thread (the even CTA's MMA issuer, the odd CTA's producer)
     auto tq_pop = [&](uint32_t k, unsigned long long &v) {
         const uint32_t slot = k % TQ;
-        if (!mbar_wait<true>(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort)) return false;
+        if (!mbar_wait<true>(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort, wl)) return false;
         v = s_tq[slot];
         mbar_arrive_cl(L_tqempty + 8 * slot);  // release (CTA scope) orders the read before the arrival
         return true;
@@ -543,7 +601,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         int ok = 0;
         if ((threadIdx.x & 31) == 0) {
             const uint32_t slot = k % TQ;
-            ok = mbar_wait<true>(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort) ? 1 : 0;
+            ok = mbar_wait<true>(b_tqfull + 8 * slot, (k / TQ) & 1, &s_abort, wl) ? 1 : 0;
             if (ok) {
                 r = s_tq[slot];
                 mbar_arrive_cl(L_tqempty + 8 * slot);  // release (CTA scope) orders the read before the arrival
@@ -596,7 +654,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 }
                 const uint32_t rb = 2 * R + rank, cb = 2 * C + rank;  // this CTA's row and column blocks
                 if (R != a_row) {
-                    if (a_loads > 0 && !mbar_wait(b_freeA, (a_loads - 1) & 1, &s_abort)) {
+                    if (a_loads > 0 && !mbar_wait(b_freeA, (a_loads - 1) & 1, &s_abort, wl)) {
                         ok = false;
                         break;
                     }
@@ -609,7 +667,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 }
                 for (uint32_t kc = 0; kc < g.nkc && ok; ++kc) {
                     for (int pl = 0; pl < P; ++pl) {
-                        if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort)) {
+                        if (!mbar_wait(b_emptyB + 8 * stage, b_phase ^ 1, &s_abort, wl)) {
                             ok = false;
                             break;
                         }
@@ -626,16 +684,38 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             }
             if (leader && ok) ok = tq_push(k, TQ_END);
             if (!ok) give_up();
-            // never leave a copy in flight: the even CTA waits for the last
-            // load into every stage (load k went to stage k % stages, in phase
-            // k / stages; the phase completes only once both CTAs' bytes have
-            // landed), and the final cluster barrier holds the odd CTA until then
-            if (leader) {
-                for (uint32_t st = 0; st < g.stages && st < loads; ++st) {
-                    const uint32_t last = loads - 1 - ((loads - 1 - st) % g.stages);
+            // Never leave a copy in flight.  Both CTAs' copies complete on the
+            // even CTA's barriers, whose phases need the even CTA's expect_tx
+            // arrival and both CTAs' bytes.  After a give-up the two producers
+            // may have started different numbers of copies (the odd one up to
+            // a ring ahead of the even one, or behind it; A row blocks at most
+            // one apart), so the odd CTA reports its counts and the even one
+            // arrives with the byte count of each copy only the odd CTA
+            // started, and cancels the expected bytes of each copy it alone
+            // started.  Then every phase up to the last copy completes once its
+            // bytes land, and the even CTA waits for them all: load k went to
+            // stage k % stages, phase k / stages.  The final cluster barrier
+            // holds the odd CTA until then.
+            if (!leader) {
+                st_cl_u32(mapa(smem_u32(&s_odd_loads[0]), 0), loads);
+                st_cl_u32(mapa(smem_u32(&s_odd_loads[1]), 0), a_loads);
+                mbar_arrive_cl_release(mapa(smem_u32(&s_odd_done), 0));
+            } else {
+                uint32_t lo = loads, ao = a_loads;
+                if (mbar_wait<true>(smem_u32(&s_odd_done), 0, nullptr)) {
+                    lo = *(volatile uint32_t *)&s_odd_loads[0];
+                    ao = *(volatile uint32_t *)&s_odd_loads[1];
+                }
+                for (uint32_t c = lo; c < loads; ++c) mbar_complete_tx(b_fullB + 8 * (c % g.stages), stage_bytes);
+                for (uint32_t c = loads; c < lo; ++c) mbar_expect_tx(b_fullB + 8 * (c % g.stages), stage_bytes);
+                if (ao < a_loads) mbar_complete_tx(b_fullA, a_bytes);
+                if (ao > a_loads) mbar_expect_tx(b_fullA, a_bytes);
+                const uint32_t nb = loads > lo ? loads : lo, na = a_loads > ao ? a_loads : ao;
+                for (uint32_t st = 0; st < g.stages && st < nb; ++st) {
+                    const uint32_t last = nb - 1 - ((nb - 1 - st) % g.stages);
                     mbar_wait(b_fullB + 8 * st, (last / g.stages) & 1, nullptr);
                 }
-                if (a_loads) mbar_wait(b_fullA, (a_loads - 1) & 1, nullptr);
+                if (na) mbar_wait(b_fullA, (na - 1) & 1, nullptr);
             }
         }
     } else if (warp == 1) {
@@ -656,14 +736,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 const uint32_t R = (uint32_t)(v >> 32);
                 if (R != a_row) {
                     if (a_loads > 0) umma2_commit_both(b_freeA);  // old A is free once issued MMAs finish
-                    if (!mbar_wait(b_fullA, a_loads & 1, &s_abort)) {
+                    if (!mbar_wait(b_fullA, a_loads & 1, &s_abort, wl)) {
                         ok = false;
                         break;
                     }
                     ++a_loads;
                     a_row = R;
                 }
-                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort)) {
+                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, &s_abort, wl)) {
                     ok = false;
                     break;
                 }
@@ -673,7 +753,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     const uint64_t a_desc = a_desc0 + kc * P * CH16;
 #pragma unroll
                     for (int pb = 0; pb < P; ++pb) {
-                        if (!mbar_wait(b_fullB + 8 * stage, b_phase, &s_abort)) {
+                        if (!mbar_wait(b_fullB + 8 * stage, b_phase, &s_abort, wl)) {
                             ok = false;
                             break;
                         }
@@ -722,7 +802,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         constexpr int NCH = TILE / EPI_ROWS / NG;   // 16-row chunks per warp and tile
         const uint32_t e = warp - 2, q = warp & 3, grp = e >> 2;
         float *snorm = epi + e * NORM_FLOATS;     // norms of this warp's rows, two buffers
-        float *stg = stage_base + grp * 2 * STG_FLOATS;  // this row group's two staging buffers (P = 2)
+        float *stg = stage_base + grp * group_floats(P);  // this row group's two staging or boundary buffers
         uint32_t hc = 0;                                   // halves staged so far (selects the buffer)
         const float tau = g.tau;
         // next tile's norms: lane l holds the norms of row l % 16 of chunks
@@ -748,14 +828,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             cur = TQ_END;
         }
         if (cur != TQ_END) prefetch(2 * (uint32_t)(cur >> 32), 2 * (uint32_t)cur + rank);
-        while (cur != TQ_END) {
+        for (;;) {
+            // this unit's accumulators; the row group goes on only if each of
+            // its warps has the unit and its accumulators (after the last
+            // unit, or after a failed wait anywhere, all four stop together)
+            const bool have = cur != TQ_END;
+            const bool got = have && warp_wait<true>(b_tfull + 8 * acc, acc_phase, &s_abort, wl);
+            if (have && !got) fail();
+            if (!named_sync_all(1 + grp, 128, got)) break;
             const uint32_t R = (uint32_t)(cur >> 32), bj = 2 * (uint32_t)cur + rank;
             unsigned long long nxt = TQ_END;
-            bool stop = false;
-            if (!warp_wait<true>(b_tfull + 8 * acc, acc_phase, &s_abort)) {
-                fail();
-                break;
-            }
             tc_fence_after();
 #pragma unroll 1
             for (uint32_t t = 0; t < 2; ++t) {
@@ -769,8 +851,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 if (t == 0) {
                     prefetch(bi + 1, bj);
                 } else if (!tq_pop_warp(k++, nxt)) {
-                    fail();
-                    stop = true;
+                    fail();  // the group stops at the next unit's vote
                     nxt = TQ_END;
                 } else if (nxt != TQ_END) {
                     prefetch(2 * (uint32_t)(nxt >> 32), 2 * (uint32_t)nxt + rank);
@@ -868,8 +949,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                             // Direct stores: for each row the warp's 32 lanes hold 32
                             // consecutive packed entries, written by one 128-byte store.
                             // For P = 3 the tensor core's operand reads already take most
-                            // of the shared-memory bandwidth, and staging (which also
-                            // costs two operand stages) measured slower.
+                            // of the shared-memory bandwidth: staging whole segments
+                            // (as P = 2 does) measured 2.51 ms against 2.23 ms, and
+                            // assembling only the 32-byte sectors that straddle two
+                            // quarters of a row 2.63 ms (N = 65536, d = 128, one
+                            // row-group barrier per unit).
+                            // The row group's four warps hold the four quarters of the
+                            // same 16 rows; a barrier before their stores keeps them
+                            // writing the same rows at the same time, so the partly
+                            // written 32-byte sectors at the quarters' edges meet in L2
+                            // soon after each other (2.24 ms with one barrier per unit,
+                            // 2.19 per tile, 2.09 per 16 rows, 2.09 per 8, 2.14 per 4).
+                            named_sync(1 + grp, 128);
                             float *row = g.out + T2(i0) + j;  // row i0, column j
                             if (bi != bj && (bi + 1) * TILE <= g.n) {
 #pragma unroll
@@ -896,7 +987,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 acc = 0;
                 acc_phase ^= 1;
             }
-            if (stop) break;
             cur = nxt;
         }
     }
@@ -1013,7 +1103,7 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.P = prec == TRI_BF16X6 ? 3 : 2;
     p.dp = (d + KCH - 1) / KCH * KCH;
     p.nkc = p.dp / KCH;
-    const size_t stg = p.P == 2 ? (size_t)(NEPI / 4) * 2 * STG_FLOATS : 0;  // P = 2 stages its stores
+    const size_t stg = (size_t)(NEPI / 4) * group_floats(p.P);  // store staging (P = 2) or boundary sectors (P = 3)
     const size_t fixed = 1024 /*align*/ + (NEPI * NORM_FLOATS + stg) * 4 + 8 * (7 + 2 * MAX_STAGES);
     const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;  // one row block per CTA
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
@@ -1134,12 +1224,13 @@ int gram_range(uint32_t n, uint32_t d, float *out, int map, int prec, void *work
     g.u0 = u0;
     g.nunits = nunits;
     g.stages = pl.stages;
-    g.tau = pl.P == 3 ? TAU_X6 : TAU_X3;
+    g.tau = flag_tau(prec, d);
     g.norms = (const float *)(ws + L.norms);
     g.out = out;
     g.flag_count = (unsigned long long *)(ws + L.hdr);
     g.status = (int *)(ws + L.hdr + 8);
     g.tile_counter = (unsigned long long *)(ws + L.hdr + 16);
+    g.wait_limit = (const unsigned long long *)(ws + L.hdr + 40);
     g.flag_list = (unsigned long long *)(ws + L.flags);
     g.flag_cap = L.cap;
     if (cudaMemsetAsync(g.tile_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return TRI_ECUDA;
@@ -1174,7 +1265,7 @@ extern "C" int tri_edm_fixup(const float *x, uint32_t n, uint32_t d, float *out,
     fixup_kernel<<<num_sms() * 4, 256, 0, s>>>(x, d, out, (const float *)(ws + L.norms),
                                                (const unsigned long long *)(ws + L.hdr),
                                                (const unsigned long long *)(ws + L.flags), L.cap,
-                                               prec == TRI_BF16X6 ? TAU_X6 : TAU_X3, n_flagged, nullptr, nullptr, 0,
+                                               flag_tau(prec, d), n_flagged, nullptr, nullptr, 0,
                                                T2(n));
     return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
@@ -1186,6 +1277,76 @@ int trihost::edm_tc(const float *x, uint32_t n, uint32_t d, float *out, int map,
     if (st == TRI_OK) st = tri_edm_gram(n, d, out, map, prec, ws, ws_bytes, s);
     if (st == TRI_OK) st = tri_edm_fixup(x, n, d, out, prec, ws, ws_bytes, n_flagged, s);
     return st;
+}
+
+// ------------------------------------------------------ split over ranks ----
+// One triangle split across processes (one per GPU): rank r computes a band
+// of whole unit rows (256 rows each, the Gram kernel's unit) whose packed
+// entries form one contiguous range of the output, so the ranks need no
+// exchange while they compute.  Band edges are placed at equal shares of the
+// n(n+1)/2 pairs: rank r's band starts at the first unit row whose packed
+// offset reaches r/ranks of the total.
+
+extern "C" int tri_edm_partition(uint32_t n, uint32_t ranks, uint32_t rank, uint32_t *row_begin, uint32_t *row_end,
+                                 uint64_t *pair_begin, uint64_t *pair_end)
+{
+    if (!row_begin || !row_end || !pair_begin || !pair_end || ranks == 0 || rank >= ranks) return TRI_EINVAL;
+    if (n > TC_MAX_N) return TRI_ERANGE;
+    const uint32_t unit = 2 * TILE, mb = (n + unit - 1) / unit;
+    const uint64_t total = T2(n);
+    // first unit row R whose start T2(min(n, 256 R)) is at least share k of the pairs
+    auto edge = [&](uint32_t k) -> uint32_t {
+        if (k >= ranks) return mb;
+        const long double target = (long double)total * k / ranks;
+        uint32_t lo = 0, hi = mb;  // smallest R in [0, mb] with T2(min(n, unit R)) >= target
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) / 2;
+            if ((long double)T2(std::min<uint64_t>(n, (uint64_t)unit * mid)) >= target) hi = mid;
+            else lo = mid + 1;
+        }
+        return lo;
+    };
+    const uint32_t R0 = edge(rank), R1 = edge(rank + 1);
+    *row_begin = (uint32_t)std::min<uint64_t>(n, (uint64_t)unit * R0);
+    *row_end = (uint32_t)std::min<uint64_t>(n, (uint64_t)unit * R1);
+    *pair_begin = T2(*row_begin);
+    *pair_end = T2(*row_end);
+    return TRI_OK;
+}
+
+extern "C" int tri_edm_rows(const float *x, uint32_t n, uint32_t d, uint32_t row_begin, uint32_t row_end,
+                            float *out_band, int map, int prec, void *workspace, size_t ws_bytes,
+                            unsigned long long *n_flagged, void *stream)
+{
+    if (!x || !out_band || n == 0 || d == 0) return TRI_EINVAL;
+    if (prec != TRI_BF16X3 && prec != TRI_BF16X6) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_BB) return TRI_EINVAL;
+    if (n > TC_MAX_N) return TRI_ERANGE;
+    const uint32_t unit = 2 * TILE;
+    if (row_begin > row_end || row_end > n) return TRI_EINVAL;
+    if (row_begin < row_end && (row_begin % unit != 0 || (row_end % unit != 0 && row_end != n))) return TRI_EINVAL;
+    if ((uintptr_t)out_band & 15) return TRI_EINVAL;
+    TcPlan pl;
+    if (!plan(d, prec, pl)) return TRI_ERANGE;
+    const WsLayout L = ws_layout(n, d, prec);
+    if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return TRI_ENOSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int r = tri_edm_prepare(x, n, d, prec, workspace, ws_bytes, s);
+    if (r != TRI_OK || row_begin == row_end) return r;
+    // The kernels index the whole packed triangle; the band's first entry,
+    // T2(row_begin) = 128 R0 (256 R0 + 1), is a multiple of 128, so the
+    // shifted base keeps out_band's 16-byte alignment.
+    const uint64_t p0 = T2(row_begin), p1 = T2(row_end);
+    float *base = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(out_band) - p0 * sizeof(float));
+    if ((r = gram_range(n, d, base, map, prec, workspace, ws_bytes, row_begin / unit,
+                        (row_end + unit - 1) / unit, s)) != TRI_OK)
+        return r;
+    char *ws = (char *)workspace;
+    fixup_kernel<<<num_sms() * 4, 256, 0, s>>>(x, d, base, (const float *)(ws + L.norms),
+                                               (const unsigned long long *)(ws + L.hdr),
+                                               (const unsigned long long *)(ws + L.flags), L.cap, flag_tau(prec, d),
+                                               n_flagged, nullptr, nullptr, p0, p1);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
 
 // ---------------------------------------------------------------- host ----
@@ -1232,35 +1393,54 @@ extern "C" int tri_edm_host(const float *x_host, uint32_t n, uint32_t d, float *
         return TRI_ECUDA;
     int r = tri_edm_prepare(x_dev, n, d, prec, workspace, ws_bytes, s);  // also zeroes both slots
     if (r != TRI_OK) return r;
+    bool queued = false;  // a copy is on the copy stream: the caller's stream must wait for it, error or not
     uint32_t R0 = 0;
-    for (uint32_t b = 0; b < bands; ++b) {
+    for (uint32_t b = 0; b < bands && r == TRI_OK; ++b) {
         uint32_t R1 = b + 1 == bands ? mb : (uint32_t)std::ceil(mb * std::sqrt((double)(b + 1) / bands));
         R1 = std::min(std::max(R1, R0 + 1), mb);
         if (R0 >= mb) break;
-        if ((r = gram_range(n, d, out_dev, map, prec, workspace, ws_bytes, R0, R1, s)) != TRI_OK) return r;
+        if ((r = gram_range(n, d, out_dev, map, prec, workspace, ws_bytes, R0, R1, s)) != TRI_OK) break;
         const uint64_t p0 = T2(std::min<uint64_t>(n, 2ull * TILE * R0)), p1 = T2(std::min<uint64_t>(n, 2ull * TILE * R1));
         fixup_kernel<<<num_sms() * 4, 256, 0, s>>>(x_dev, d, out_dev, (const float *)(ws + L.norms),
                                                    (const unsigned long long *)(ws + L.hdr),
                                                    (const unsigned long long *)(ws + L.flags), L.cap,
-                                                   prec == TRI_BF16X6 ? TAU_X6 : TAU_X3, n_flagged, slot + (b & 1),
+                                                   flag_tau(prec, d), n_flagged, slot + (b & 1),
                                                    slot + ((b + 1) & 1), p0, p1);
-        if (cudaGetLastError() != cudaSuccess) return TRI_ECUDA;
+        if (cudaGetLastError() != cudaSuccess) {
+            r = TRI_ECUDA;
+            break;
+        }
         // the band's rows are final: copy them while the next band computes
         cudaEvent_t ev;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return TRI_ECUDA;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            r = TRI_ECUDA;
+            break;
+        }
         cudaError_t e = cudaEventRecord(ev, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
         cudaEventDestroy(ev);
-        if (e == cudaSuccess && p1 > p0)
+        if (e == cudaSuccess && p1 > p0) {
             e = cudaMemcpyAsync(out_host + p0, out_dev + p0, (p1 - p0) * sizeof(float), cudaMemcpyDeviceToHost, cs);
-        if (e != cudaSuccess) return TRI_ECUDA;
+            queued = queued || e == cudaSuccess;
+        }
+        if (e != cudaSuccess) r = TRI_ECUDA;
         R0 = R1;
     }
-    // the caller's stream completes only after the last copy
+    if (!queued) return r;
+    // the caller's stream completes only after the last copy (also after an
+    // error, so that the caller may free or reuse the buffers once it has
+    // synchronised its stream)
     cudaEvent_t done;
-    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) return TRI_ECUDA;
-    cudaError_t e = cudaEventRecord(done, cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done, 0);
-    cudaEventDestroy(done);
-    return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
+    cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        e = cudaEventRecord(done, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done, 0);
+        cudaEventDestroy(done);
+    }
+    if (e != cudaSuccess) {
+        // cannot order the streams: wait for the copies here instead
+        cudaStreamSynchronize(cs);
+        if (r == TRI_OK) r = TRI_ECUDA;
+    }
+    return r;
 }

@@ -60,6 +60,8 @@ _SIGS = {
     "tri_edm_gram": ([_u32, _u32, _vp, _i32, _i32, _vp, _sz, _vp], _i32),
     "tri_edm_fixup": ([_vp, _u32, _u32, _vp, _i32, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_host": ([_vp, _u32, _u32, _vp, _i32, _i32, _u32, _vp, _vp, _vp, _sz, _vp, _vp], _i32),
+    "tri_edm_partition": ([_u32, _u32, _u32, _vp, _vp, _vp, _vp], _i32),
+    "tri_edm_rows": ([_vp, _u32, _u32, _u32, _u32, _vp, _i32, _i32, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_batched": ([_vp, _vp, _vp, _u32, _u32, _vp, _vp, _u32, _u32, _vp, _sz, _vp], _i32),
     "tri_edm_batched_workspace_size": ([_u32, _szp], _i32),
     "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
@@ -207,6 +209,22 @@ def tri_edm_fixup(x, out, prec: int, workspace, n_flagged=None, stream=None) -> 
     n, d = x.shape
     _check("tri_edm_fixup", _lib.tri_edm_fixup(_ptr(x), n, d, _ptr(out), prec, _ptr(workspace),
                                                _nbytes(workspace), _ptr(n_flagged), _stream(stream)))
+
+
+def tri_edm_partition(n: int, ranks: int, rank: int):
+    """(row_begin, row_end, pair_begin, pair_end) of rank `rank` of `ranks` (host only)."""
+    rb, re_, pb, pe = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check("tri_edm_partition", _lib.tri_edm_partition(n, ranks, rank, ctypes.byref(rb), ctypes.byref(re_),
+                                                       ctypes.byref(pb), ctypes.byref(pe)))
+    return rb.value, re_.value, pb.value, pe.value
+
+
+def tri_edm_rows(x, row_begin: int, row_end: int, out_band, map: int = MAP_LAMBDA, prec: int = BF16X6,
+                 workspace=None, n_flagged=None, stream=None) -> None:
+    n, d = x.shape
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("tri_edm_rows", _lib.tri_edm_rows(_ptr(x), n, d, row_begin, row_end, _ptr(out_band), map, prec,
+                                             _ptr(workspace), ws_bytes, _ptr(n_flagged), _stream(stream)))
 
 
 def tri_edm_batched_workspace_size(count: int) -> int:
