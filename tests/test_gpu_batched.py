@@ -44,17 +44,17 @@ def test_batched_matches_oracle(orc, rho, reg):
         assert rel_err(got, orc.edm_packed(xk)) <= 1e-5, k
 
 
-def test_batched_thousand_instances_sampled(orc):
-    # the 1000-instance batch (N log-uniform in [64, 8192], d = 64), checked on
-    # sampled pairs of every instance
+def test_batched_thousand_instances_every_pair(orc):
+    # the 1000-instance batch (N log-uniform in [64, 8192], d = 64, seed 1609):
+    # every pair of every instance against the FP64 oracle, at rho = 32 (the
+    # bench's launch) and rho = 16
     t = tri()
     sizes = inputs.batched_sizes(1000, seed=1609)
-    x, pt_off, out_off, o = _batched(t, sizes, 64, 16, 4, seed=1609)
-    rng = np.random.default_rng(1)
+    runs = [_batched(t, sizes, 64, rho, 4, seed=1609) for rho in (32, 16)]
+    x, pt_off, out_off, _ = runs[0]
     for k, nk in enumerate(sizes):
         nk = int(nk)
-        pi = rng.integers(0, nk, 64)
-        pj = (rng.random(64) * (pi + 1)).astype(np.int64)
-        xk = x[int(pt_off[k]): int(pt_off[k]) + nk]
-        got = o[int(out_off[k]) + pi * (pi + 1) // 2 + pj]
-        assert rel_err(got, orc.edm_pairs(xk, pi, pj)) <= 1e-5, k
+        ref = orc.edm_packed(x[int(pt_off[k]): int(pt_off[k]) + nk])
+        for rho, (_, _, _, o) in zip((32, 16), runs):
+            got = o[int(out_off[k]): int(out_off[k]) + nk * (nk + 1) // 2]
+            assert rel_err(got, ref) <= 1e-5, (rho, k)

@@ -90,3 +90,16 @@ def test_ca_hundred_steps(orc):
     ref = orc.ca_run(g, 100)
     for m, rho in ((t.MAP_LAMBDA, 16), (t.MAP_BB, 16), (t.MAP_LAMBDA, 32), (t.MAP_RB, 8)):
         assert np.array_equal(_run(t, g, n, 100, m, rho), ref)
+
+
+def test_ca_c1_hundred_steps_full_size(orc):
+    # the Life workload as configured: the n = 16384 triangle, Bernoulli(0.5)
+    # cells, 100 synchronous steps, every cell bit-exact after the last step,
+    # under lambda and the bounding box at the tile the bench times (rho = 32)
+    t = tri()
+    n = 16384
+    g = inputs.ca_grid(n, seed=1609)
+    ref = orc.ca_run(g, 100)
+    for m in (t.MAP_LAMBDA, t.MAP_BB):
+        got = _run(t, g, n, 100, m, 32)
+        assert np.array_equal(got, ref), m

@@ -4,10 +4,11 @@ against the FP64 oracle, element by element.
 Tolerance: relative error <= 1e-5 per distance for the three-plane split
 (BF16X6), exact zeros for the diagonal and duplicated points.  The bound
 behind it: the split is exact, the dropped products are below 2^-23 |x_i||x_j|
-in sum, and 48 FP32 accumulation steps add at most 48*2^-23 of the magnitude
-sum, so |error of d^2| <= 6.2e-6 (|x_i|^2 + |x_j|^2); pairs whose estimate of
-d^2 is below tau = 0.3125 (|x_i|^2 + |x_j|^2) are recomputed in FP64, which
-leaves every other pair within 6.2e-6 / (2 * 0.3125) ~ 1e-5.  The two-plane
+in sum, and each of the 24 FP32 accumulation steps per 64-wide K chunk adds at
+most 2^-23 of the magnitude sum, so |error of d^2| <= (2 + 24 nkc) 2^-23
+(|x_i|^2 + |x_j|^2) for nkc = ceil(d / 64) chunks; pairs whose estimate of d^2
+is below tau = (2 + 24 nkc) 2^-23 / 1.96e-5 times (|x_i|^2 + |x_j|^2) are
+recomputed in FP64, which leaves every other pair within 1e-5.  The two-plane
 split (BF16X3) carries no such guarantee; its measured error is checked
 against 1e-4.
 """
@@ -57,6 +58,41 @@ def test_tc_edm_small(orc, prec, tol, mapname):
         assert nflag >= len(inputs.duplicate_pairs(x))
 
 
+def test_tc_edm_near_cancellation_d192(orc):
+    # d = 192 (three K chunks, the BF16X6 limit), large norms: pairs that
+    # differ in one coordinate by a few ulps (the flag path must decide them),
+    # and pairs spread over d^2 / (|x_i|^2 + |x_j|^2) in [0.3, 0.7], around the
+    # flag threshold (0.45 at three chunks), where unflagged pairs sit closest
+    # to the error bound
+    t = tri()
+    n, d = 600, 192
+    rng = np.random.default_rng(192)
+    base = (rng.standard_normal((n // 3, d)) * 50.0).astype(np.float32)
+    x = np.empty((n, d), dtype=np.float32)
+    x[0::3] = base
+    near = base.copy()
+    k = rng.integers(0, d, n // 3)
+    rows = np.arange(n // 3)
+    near[rows, k] = np.nextafter(near[rows, k], np.float32(np.inf))
+    near[rows, (k + 1) % d] = np.nextafter(np.nextafter(near[rows, (k + 1) % d], np.float32(-np.inf)),
+                                           np.float32(-np.inf))
+    x[1::3] = near
+    # ratio r = d^2 / (|a|^2 + |b|^2) for b = c a + s z (z orthogonal to a, |z| = |a|):
+    # r = ((1 - c)^2 + s^2) / (1 + c^2 + s^2); c = sqrt(1 - s^2) keeps |b| = |a|,
+    # so r = 1 - c, spread over [0.3, 0.7]
+    z = rng.standard_normal((n // 3, d))
+    a = base.astype(np.float64)
+    z -= (np.sum(z * a, axis=1) / np.sum(a * a, axis=1))[:, None] * a
+    z *= (np.linalg.norm(a, axis=1) / np.linalg.norm(z, axis=1))[:, None]
+    c = 1.0 - np.linspace(0.3, 0.7, n // 3)
+    sn = np.sqrt(1.0 - c * c)
+    x[2::3] = (c[:, None] * a + sn[:, None] * z).astype(np.float32)
+    got, nflag = _run(t, x, t.BF16X6, t.MAP_LAMBDA)
+    ref = orc.edm_packed(x)
+    assert rel_err(got, ref) <= 1e-5
+    assert nflag >= n // 3
+
+
 def test_tc_edm_uniform_low_d(orc):
     # few features in [0,1): large norms relative to distances -> many flags
     t = tri()
@@ -103,6 +139,129 @@ def test_tc_edm_full_size_sampled(orc):
         assert int(ws[8:12].view(torch.int32).item()) == 0
         assert rel_err(out[idx].cpu().numpy(), ref) <= tol, prec
         assert int(nf.item()) >= len(dup)
+
+
+def _full_compare(orc, x, outs, bands=16):
+    """Every pair of the packed triangle of each host array in `outs` against
+    the FP64 oracle, in row bands of equal pair count.  Returns, per array,
+    the maximum and the 99.99th percentile relative error (from a histogram
+    of log10 errors at 0.001 resolution), the exact zeros of the reference and
+    whether the array matched them all.  The comparison runs on several host
+    threads (numpy releases the interpreter lock in its loops)."""
+    import concurrent.futures as cf
+    import os
+    n = x.shape[0]
+    edges = [0] + [min(n, int(np.ceil(n * np.sqrt(b / bands)))) for b in range(1, bands)] + [n]
+    bins = np.linspace(-12.0, -2.0, 10001)
+
+    def part(o, ref, p0, a, b):
+        r = ref[a:b]
+        got = o[p0 + a:p0 + b].astype(np.float64)
+        z = r == 0
+        zok = bool(np.all(got[z] == 0.0))
+        nz = ~z
+        rel = np.abs(got[nz] - r[nz]) / r[nz]
+        pos = rel > 0
+        h = np.histogram(np.log10(rel[pos]), bins=bins)[0]
+        return (float(rel.max()) if rel.size else 0.0, h, int(rel.size - np.count_nonzero(pos)), zok,
+                int(np.count_nonzero(z)))
+
+    st = [{"max": 0.0, "hist": np.zeros(len(bins) - 1, dtype=np.int64), "under": 0, "zeros_ok": True}
+          for _ in outs]
+    zeros = 0
+    step = 1 << 23
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        for r0, r1 in zip(edges[:-1], edges[1:]):
+            if r1 <= r0:
+                continue
+            ref = orc.edm_rows(x, r0, r1)
+            p0 = r0 * (r0 + 1) // 2
+            for oi, (o, s) in enumerate(zip(outs, st)):
+                for mx, h, under, zok, nzero in ex.map(lambda ab: part(o, ref, p0, *ab),
+                                                       [(a, min(a + step, len(ref))) for a in range(0, len(ref), step)]):
+                    s["max"] = max(s["max"], mx)
+                    s["hist"] += h
+                    s["under"] += under
+                    s["zeros_ok"] &= zok
+                    if oi == 0:
+                        zeros += nzero
+    total = n * (n + 1) // 2 - zeros
+    res = []
+    for s in st:
+        # the error that 0.01% of the nonzero pairs exceed (upper edge of its bin)
+        need = int(np.ceil(1e-4 * total))
+        c = np.cumsum(s["hist"][::-1])
+        k = int(np.searchsorted(c, need))
+        p9999 = 10.0 ** bins[len(bins) - 1 - k] if k < len(c) else 0.0
+        res.append({"max_rel": s["max"], "p99_99_rel": p9999, "exact_zero_pairs": zeros,
+                    "zeros_ok": s["zeros_ok"], "exact_pairs": s["under"]})
+    return res
+
+
+def test_tc_edm_full_triangle_every_pair(orc):
+    # the launch the bench times (N = 65536, d = 128, 1% duplicated rows, seed
+    # 1609): all 2,147,516,416 pairs of the BF16X6 and BF16X3 triangles against
+    # the FP64 oracle, with the per-result error stated (pytest -s prints it)
+    import json
+    import torch
+    t = tri()
+    n, d = 65536, 128
+    x = inputs.edm_normal_points(n, d, seed=1609, dup_frac=0.01)
+    D = dev()
+    xd = torch.from_numpy(x).to(D)
+    out = torch.empty(n * (n + 1) // 2, dtype=torch.float32, device=D)
+    hosts, flags = [], []
+    for prec in (t.BF16X6, t.BF16X3):
+        ws = torch.empty(t.tri_edm_workspace_size(n, d, prec), dtype=torch.uint8, device=D)
+        nf = torch.zeros(1, dtype=torch.int64, device=D)
+        t.tri_edm(xd, out, map=t.MAP_LAMBDA, prec=prec, workspace=ws, n_flagged=nf)
+        torch.cuda.synchronize()
+        assert int(ws[8:12].view(torch.int32).item()) == 0
+        hosts.append(out.cpu().numpy())
+        flags.append(int(nf.item()))
+        del ws
+    del out, xd
+    torch.cuda.empty_cache()
+    res = _full_compare(orc, x, hosts)
+    for r, nf, name in zip(res, flags, ("bf16x6", "bf16x3")):
+        r["n_flagged"] = nf
+        print(f"full-triangle error {name}: " + json.dumps(r))
+    assert res[0]["zeros_ok"] and res[1]["zeros_ok"]
+    assert res[0]["max_rel"] <= 1e-5, res[0]
+    assert res[1]["max_rel"] <= 1e-4, res[1]
+    assert flags[0] >= len(inputs.duplicate_pairs(x))
+
+
+@pytest.mark.parametrize("prec", ["BF16X6", "BF16X3"])
+def test_tc_gram_wait_limit_runs_out_cleanly(orc, prec):
+    # The Gram kernel's waits between its roles (copy, MMA, epilogue) are
+    # bounded.  The workspace word at byte 40 shortens that bound (here to
+    # 1 ns): the waits give up, both CTAs of every pair stop, drain the copies
+    # and MMAs in flight, free their tensor memory and return, and the status
+    # word (int at byte 8) reads TRI_ETIMEOUT.  The same workspace then gives
+    # the right triangle on a normal call (tri_edm_prepare clears the header).
+    import torch
+    t = tri()
+    p = getattr(t, prec)
+    D = dev()
+    n, d = 1000, 100
+    x = inputs.edm_normal_points(n, d, seed=41, dup_frac=0.02)
+    xd = torch.from_numpy(x).to(D)
+    size = n * (n + 1) // 2
+    out = torch.full((size + 64,), -7.0, dtype=torch.float32, device=D)
+    ws = torch.empty(t.tri_edm_workspace_size(n, d, p), dtype=torch.uint8, device=D)
+    for _ in range(2):
+        t.tri_edm_prepare(xd, p, ws)
+        ws[40:48].view(torch.int64).fill_(1)
+        t.tri_edm_gram(n, d, out, t.MAP_LAMBDA, p, ws)
+        assert t.tri_sync_status(ws[8:12].view(torch.int32)) == t.TRI_ETIMEOUT
+    assert torch.all(out[size:] == -7.0)
+    nf = torch.zeros(1, dtype=torch.int64, device=D)
+    t.tri_edm(xd, out, map=t.MAP_LAMBDA, prec=p, workspace=ws, n_flagged=nf)
+    assert t.tri_sync_status(ws[8:12].view(torch.int32)) == t.TRI_OK
+    o = out.cpu().numpy()
+    assert np.all(o[size:] == -7.0)
+    assert rel_err(o[:size], orc.edm_packed(x)) <= (1e-5 if prec == "BF16X6" else 1e-4)
 
 
 def test_tc_phases_and_errors():
@@ -184,6 +343,49 @@ def test_tc_edm_host_list_overflow_per_band(orc):
     torch.cuda.synchronize()
     assert int(nf.item()) > 1 << 20
     assert rel_err(oh.numpy(), orc.edm_packed(x)) <= 1e-5
+
+
+@pytest.mark.parametrize("ranks", [1, 3, 8])
+def test_tc_edm_rows_bands_assemble_the_triangle(ranks):
+    # one triangle split across ranks (tri_edm_partition): each rank's band,
+    # computed by tri_edm_rows into its own buffer, holds the same bytes as
+    # that range of tri_edm's output (the ranks run here one after another)
+    import torch
+    t = tri()
+    D = dev()
+    n, d = 3000, 64
+    x = inputs.edm_normal_points(n, d, seed=78, dup_frac=0.02)
+    xd = torch.from_numpy(x).to(D)
+    size = n * (n + 1) // 2
+    for prec in (t.BF16X6, t.BF16X3):
+        ws = torch.empty(t.tri_edm_workspace_size(n, d, prec), dtype=torch.uint8, device=D)
+        ref = torch.empty(size, device=D)
+        t.tri_edm(xd, ref, prec=prec, workspace=ws)
+        parts = []
+        for r in range(ranks):
+            rb, re_, pb, pe = t.tri_edm_partition(n, ranks, r)
+            band = torch.full((pe - pb + 16,), -5.0, device=D)
+            t.tri_edm_rows(xd, rb, re_, band, prec=prec, workspace=ws)
+            torch.cuda.synchronize()
+            assert int(ws[8:12].view(torch.int32).item()) == 0
+            assert torch.all(band[pe - pb:] == -5.0), "store past the band"
+            parts.append(band[:pe - pb])
+        assert torch.equal(torch.cat(parts), ref), (prec, ranks)
+
+
+def test_tc_edm_rows_errors():
+    import torch
+    t = tri()
+    D = dev()
+    x = torch.zeros(600, 8, device=D)
+    ws = torch.empty(t.tri_edm_workspace_size(600, 8, t.BF16X6), dtype=torch.uint8, device=D)
+    band = torch.empty(600 * 601 // 2, device=D)
+    for rb, re_ in ((100, 256), (0, 300), (256, 601), (300, 200)):  # not on unit rows / past n / reversed
+        with pytest.raises(t.TriError) as e:
+            t.tri_edm_rows(x, rb, re_, band, workspace=ws)
+        assert e.value.status == t.TRI_EINVAL
+    t.tri_edm_rows(x, 600, 600, band, workspace=ws)  # an empty band is allowed
+    torch.cuda.synchronize()
 
 
 def test_tc_edm_host_errors():
