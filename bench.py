@@ -12,10 +12,13 @@ end-to-end figure through host buffers, and the CPU oracle timed on a bounded
 sample on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--prec fp32|bf16x3|bf16x6]
+                  [--prec fp32|bf16x3|bf16x6] [--split] [--suite]
 
 With N > 1 (torchrun), every rank runs its own full instance of the workload
-(weak scaling, no collective on the data path); rank 0 prints the line.
+(weak scaling, no collective on the data path); rank 0 prints the line.  With
+--split the ranks share one triangle instead, each computing a band of rows
+of equal pair count (strong scaling).  --suite prints one line per other
+hot-path row (maps, FP32 EDM, Life, Axilrod-Teller, collisions, batched EDM).
 """
 from __future__ import annotations
 
@@ -117,10 +120,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------ reference arm -------
-def cpu_oracle_sample(x: np.ndarray, target_s: float = 12.0):
+def cpu_oracle_sample(x: np.ndarray, target_s: float = 12.0, with_time: bool = False):
     """Time the CPU oracle on a band of full rows at the end of the triangle.
 
-    Returns (pairs/s, threads, sample description)."""
+    Returns (pairs/s, threads, sample description[, seconds of the timed band])."""
     import oracle
     n = x.shape[0]
     probe = 64
@@ -135,7 +138,23 @@ def cpu_oracle_sample(x: np.ndarray, target_s: float = 12.0):
     oracle.edm_rows(x, r0, n)
     dt = time.perf_counter() - t0
     pairs = (n * (n + 1) - r0 * (r0 + 1)) // 2
-    return pairs / dt, oracle.threads(), f"rows [{r0}, {n}) of the triangle: {pairs} pairs in {dt:.2f} s"
+    desc = f"rows [{r0}, {n}) of the triangle: {pairs} pairs in {dt:.2f} s"
+    if with_time:
+        return pairs / dt, oracle.threads(), desc, dt
+    return pairs / dt, oracle.threads(), desc
+
+
+def headline_config(prec: str) -> dict:
+    """The workload the headline line (and the reference arm beside it) runs."""
+    P = N_PTS * (N_PTS + 1) // 2
+    return {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP, "map": "lambda",
+            "tile": (("16x16 threads x 8x8 pairs" if D_FEAT >= 32 else "16x16 threads x 4x4 pairs")
+                     if prec == "fp32"
+                     else "2x2 blocks of 128x128 tiles per CTA pair (tcgen05.mma.cta_group::2, M=N=256)"),
+            "prec": prec, "pairs_per_step": P,
+            "l2": (f"each step writes the {4 * P / 1e9:.2f} GB triangle (> 129 MB L2), which flushes L2 "
+                   "between steps" if 4 * P > 129e6 else
+                   f"the {4 * P / 1e6:.1f} MB triangle fits in L2: no flush between steps")}
 
 
 def max_over_ranks(values, world: int, device=None):
@@ -163,22 +182,86 @@ def run_reference(args, rank: int, world: int):
     from paper_1609_01490_gb300 import inputs
     x = inputs.edm_normal_points(N_PTS, D_FEAT, seed=1609, dup_frac=DUP)
     total_pairs = N_PTS * (N_PTS + 1) // 2
-    vals = []
+    vals, secs = [], []
     for s in range(args.warmup + args.steps):
-        rate, thr, sample = cpu_oracle_sample(x, target_s=8.0)
+        rate, thr, sample, dt = cpu_oracle_sample(x, target_s=8.0, with_time=True)
         if s >= args.warmup:
             vals.append(rate)
+            secs.append(dt)
     value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": "pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_pairs / value,
+        "steps": args.steps, "warmup": args.warmup,
+        # each step is one bounded band of rows, timed as run (not the whole triangle)
+        "ms_per_step": 1e3 * statistics.median(secs),
+        "ms_per_step_note": "wall time of one step's band of rows; the whole triangle would take "
+                            f"{1e3 * total_pairs / value:.0f} ms at this rate",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP,
-                   "note": "CPU oracle (FP64 direct differences), each step a bounded band of rows"},
+        "config": headline_config("bf16x6"),
+        "impl_note": "CPU oracle (FP64 direct differences), each step a bounded band of rows",
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": thr, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def graph_time_ms(fn, reps, stream):
+    """Mean ms of fn, captured `reps` times into one CUDA graph, best of 3 replays
+    timed with CUDA events on `stream`."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(stream)
+    with torch.cuda.stream(s2):
+        fn()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s2):
+            for _ in range(reps):
+                fn()
+    stream.wait_stream(s2)
+    g.replay()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b) / reps)
+    return best
+
+
+def paper_comparison(tri, inputs, dev, stream):
+    """The paper's own comparison (Section 5) on this GPU, beside the headline:
+    the paper-size EDM (N = 2048, d = 3, one pair per thread, rho = 16, as the
+    paper launches it) and one triangular Life step at n = 16384 (rho = 32),
+    under lambda, the bounding box and the rectangular box.  Each time is the
+    mean of many launches captured in one CUDA graph; I = t_BB / t_map."""
+    import torch
+    out = {}
+    x = torch.from_numpy(inputs.edm_uniform_points(2048, 3, seed=1609)).to(dev)
+    o = torch.empty(2048 * 2049 // 2, dtype=torch.float32, device=dev)
+    t = {nm: graph_time_ms(lambda: tri.tri_edm(x, o, map=m, rho=16, reg=1), 200, stream)
+         for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB))}
+    out["edm_n2048_d3_rho16_reg1"] = {"ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()}}
+    n = 16384
+    a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)
+    b = torch.zeros_like(a)
+
+    def life(m):
+        def run():
+            for k in range(10):
+                src, dst = (a, b) if k % 2 == 0 else (b, a)
+                tri.tri_ca_step(src, dst, n, map=m, rho=32)
+        return run
+    t = {nm: graph_time_ms(life(m), 1, stream) / 10
+         for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB))}
+    out["life_n16384_step_rho32"] = {"ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()}}
+    del x, o, a, b
+    return out
 
 
 # ------------------------------------------------------------ row suite -----
@@ -198,30 +281,7 @@ def run_suite(args):
     stream = torch.cuda.current_stream()
 
     def graph_ms(fn, reps):
-        """Mean ms of fn, captured `reps` times into one CUDA graph, replayed 3 times."""
-        fn()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        s2 = torch.cuda.Stream()
-        s2.wait_stream(stream)
-        with torch.cuda.stream(s2):
-            fn()
-            torch.cuda.synchronize()
-            with torch.cuda.graph(g, stream=s2):
-                for _ in range(reps):
-                    fn()
-        stream.wait_stream(s2)
-        g.replay()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(3):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            g.replay()
-            b.record(stream)
-            torch.cuda.synchronize()
-            best = min(best, a.elapsed_time(b) / reps)
-        return best
+        return graph_time_ms(fn, reps, stream)
 
     only = set(args.only.split(",")) if args.only else None
 
@@ -513,6 +573,80 @@ def run_suite(args):
                                       "the first 20 instances, FP64")})
 
 
+def run_split(args, rank: int, world: int, local: int):
+    """One triangle split across the ranks (--split): rank r computes the band
+    of rows tri_edm_partition gives it (equal pair counts, disjoint packed
+    ranges, no exchange while computing) with tri_edm_rows; the job's value is
+    the triangle's pairs over the slowest rank's time (strong scaling).  The
+    bands stay on their GPUs: gathering them is not part of the EDM."""
+    import torch
+    import torch.distributed as dist
+    from paper_1609_01490_gb300 import inputs
+    from paper_1609_01490_gb300 import tri
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    prec = {"bf16x3": tri.BF16X3, "bf16x6": tri.BF16X6}[args.prec]
+    x_host = inputs.edm_normal_points(N_PTS, D_FEAT, seed=1609, dup_frac=DUP)  # the same points on every rank
+    P = N_PTS * (N_PTS + 1) // 2
+    rb, re_, pb, pe = tri.tri_edm_partition(N_PTS, world, rank)
+    x = torch.from_numpy(x_host).to(dev)
+    band = torch.empty(max(pe - pb, 4), dtype=torch.float32, device=dev)
+    ws = torch.empty(tri.tri_edm_workspace_size(N_PTS, D_FEAT, prec), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        tri.tri_edm_rows(x, rb, re_, band, map=tri.MAP_LAMBDA, prec=prec, workspace=ws)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return e0.elapsed_time(e1) / k
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms = max_over_ranks([timed(step, args.steps, args.warmup)], world, dev)[0]
+    clocks = sampler.stop()
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        bh = torch.empty(band.numel(), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            x.copy_(xh, non_blocking=True)
+            step()
+            bh.copy_(band, non_blocking=True)
+        ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), 1)], world, dev)[0]
+        e2e = {"value": P / (ms_e2e * 1e-3), "ms_per_step": ms_e2e, "unit": "pairs/s",
+               "h2d_bytes_per_step": xh.numel() * 4, "d2h_bytes_per_step": (pe - pb) * 4,
+               "path": "copies around tri_edm_rows (each rank's band)"}
+    cfg = headline_config(args.prec)
+    cfg["parallelism"] = f"one triangle split in {world} row bands of equal pair count (tri_edm_partition)"
+    line = {"metric": "pairs/s", "value": P / (ms * 1e-3), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": cfg, "clocks": clocks,
+            "gpu_launches": args.steps * 3, "band": {"rows": [rb, re_], "pairs": pe - pb}}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
     # -------------------------------------------------------------- our arm -----
 
 
@@ -527,6 +661,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--no-arms", action="store_true", help="skip the BB and FP32 comparison arms")
+    ap.add_argument("--split", action="store_true",
+                    help="split one triangle across the ranks in row bands (strong scaling) instead of "
+                         "one triangle per rank (weak scaling, the default)")
     ap.add_argument("--n", type=int, default=N_PTS, help="points (smaller cases are for profiling only)")
     ap.add_argument("--d", type=int, default=D_FEAT, help="features (smaller cases are for profiling only)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per other hot-path row instead")
@@ -544,6 +681,11 @@ def main():
         return
     if args.suite:
         run_suite(args)
+        return
+    if args.split:
+        if args.prec == "fp32":
+            ap.error("--split runs the tensor-core path (bf16x3 or bf16x6)")
+        run_split(args, rank, world, local)
         return
     if (args.n, args.d) != (N_PTS, D_FEAT):
         N_PTS, D_FEAT = args.n, args.d
@@ -637,6 +779,8 @@ def main():
     else:
         ms_fp32 = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_LAMBDA, tri.FP32), 3, 1)
     ms_bb, ms_fp32 = max_over_ranks([ms_bb, ms_fp32], world, dev)
+    # ---- the paper's comparison of maps at its own sizes (outside the timed region)
+    paper = None if args.no_arms else paper_comparison(tri, inputs, dev, stream)
 
     # ---- roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -657,8 +801,10 @@ def main():
         # algorithmic bytes: the packed FP32 triangle written once, the planes and norms read once
         nbytes = 4.0 * P + planes * N_PTS * dp * 2 + 4 * N_PTS
         hbm = nbytes / t_gram / 1e9
-        tiles = (-(-N_PTS // 128)) * (-(-N_PTS // 128) + 1) // 2
-        tflop = 2.0 * dp * nprod * tiles * 128 * 128 / t_gram / 1e12
+        # algorithmic tensor work: every pair i >= j once, 2 flop per
+        # multiply-add over the K-padded features, for each kept plane product
+        flops = 2.0 * dp * nprod * P
+        tflop = flops / t_gram / 1e12
         traffic = NCU_TRAFFIC.get((args.prec, N_PTS, D_FEAT))
         roof_hbm = {"bound": "hbm", "kernel": f"gram_kernel<lambda,{planes}>", "achieved": hbm,
                     "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": hbm / float(peaks["hbm_gbs"]),
@@ -667,7 +813,7 @@ def main():
         roof_tc = {"bound": "tensor", "kernel": f"gram_kernel<lambda,{planes}>", "achieved": tflop,
                    "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                    "frac": tflop / float(peaks["bf16_tflops"]), "traffic": traffic,
-                   "flops": 2.0 * dp * nprod * tiles * 128 * 128,
+                   "flops": flops, "flops_note": "N(N+1)/2 pairs x 2 x K(padded) x plane products",
                    "peak_source": f"bf16_tflops (burst) of {peak_src}"}
         roof, roof_alt = (roof_hbm, roof_tc) if roof_hbm["frac"] >= roof_tc["frac"] else (roof_tc, roof_hbm)
 
@@ -702,17 +848,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16", "bf16x6": "bf16"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_PTS, "d": D_FEAT, "dup_frac": DUP, "map": "lambda",
-                   "tile": (("16x16 threads x 8x8 pairs" if D_FEAT >= 32 else "16x16 threads x 4x4 pairs")
-                            if prec == tri.FP32
-                            else "2x2 blocks of 128x128 tiles per CTA pair (tcgen05.mma.cta_group::2, M=N=256)"),
-                   "prec": args.prec, "pairs_per_step": P,
-                   "l2": (f"each step writes the {4 * P / 1e9:.2f} GB triangle (> 129 MB L2), which flushes L2 "
-                          "between steps" if 4 * P > 129e6 else
-                          f"the {4 * P / 1e6:.1f} MB triangle fits in L2: no flush between steps")},
+        "config": headline_config(args.prec),
         "bb": {"ms_per_step": ms_bb, "value": job_rate(world, P, ms_bb), "I_bb_over_lambda": ms_bb / ms_step},
         "fp32_lambda": {"ms_per_step": ms_fp32, "value": job_rate(world, P, ms_fp32),
                         "speedup_of_headline": ms_fp32 / ms_step},
+        "paper_maps": paper,
         "clocks": clocks,
         "gpu_launches": args.steps * (1 if prec == tri.FP32 else 3),
         "roofline": roof,
