@@ -14,9 +14,15 @@ Kernels and their candidate maps:
   ca:  lambda, lambda on P_Delta, BB, RB, REC (one Life step)
   at:  tetrahedral lambda, BB (Axilrod-Teller energy)
 REC is skipped where the block count is not a power of two.
+
+The batched EDM (many uneven triangles in one persistent launch, lambda on
+each instance's blocks) has one map and is tuned over its tile instead:
+rho in {8, 16, 32} threads per side times reg x reg pairs per thread
+(``tune_batched``).
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 import statistics
@@ -132,6 +138,73 @@ def best(kernel: str, n: int, d: int = 1, **kw):
     mname, rho = name.split("/")
     inv = {v: k for k, v in tri.MAP_NAMES.items()}
     return inv[mname], int(rho), res[name]
+
+
+# (rho, reg) tiles of the batched launch: reg x reg pairs per thread, 8 x 8 only with rho <= 16
+BATCHED_TILES = tuple((r, g) for r in RHOS for g in (1, 2, 4, 8) if not (g == 8 and r > 16))
+
+
+class _Batched:
+    """Device buffers of one batch (instances of sizes `sizes`, d features each)."""
+
+    def __init__(self, sizes, d: int, seed: int):
+        dev = torch.device("cuda")
+        sizes = np.asarray(sizes, dtype=np.uint32)
+        x, pt_off = inputs.batched_points(sizes, d, seed=seed)
+        tri_len = sizes.astype(np.int64) * (sizes.astype(np.int64) + 1) // 2
+        out_off = np.zeros(len(sizes), dtype=np.uint64)
+        out_off[1:] = np.cumsum(tri_len)[:-1]
+        self.x = torch.from_numpy(x).to(dev)
+        self.pt_off = torch.from_numpy(pt_off.view(np.int64)).to(dev)
+        self.n_k = torch.from_numpy(sizes.astype(np.int32)).to(dev)
+        self.out_off = torch.from_numpy(out_off.view(np.int64)).to(dev)
+        self.out = torch.empty(max(int(tri_len.sum()), 1), dtype=torch.float32, device=dev)
+        self.ws = torch.empty(tri.tri_edm_batched_workspace_size(len(sizes)) // 8 + 1, dtype=torch.int64, device=dev)
+
+    def launch(self, rho: int, reg: int):
+        tri.tri_edm_batched(self.x, self.pt_off, self.n_k, self.out, self.out_off, rho=rho, reg=reg,
+                            workspace=self.ws)
+
+
+def tune_batched(sizes, d: int, reps: int = 5, seed: int = 1609, use_cache: bool = True,
+                 tiles=BATCHED_TILES) -> dict:
+    """{"rho/reg": median ms} of the batched launch over every tile, on one
+    seeded batch of instances of the given sizes."""
+    sizes = np.asarray(sizes, dtype=np.uint32)
+    digest = hashlib.sha1(sizes.tobytes()).hexdigest()[:16]
+    key = f"{torch.cuda.get_device_name()}|batched|{len(sizes)}|{digest}|{d}"
+    cache = load_cache() if use_cache else {}
+    if key in cache:
+        return cache[key]
+    work = _Batched(sizes, d, seed)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for rho, reg in tiles:
+        for _ in range(2):
+            work.launch(rho, reg)
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            work.launch(rho, reg)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        res[f"{rho}/{reg}"] = float(statistics.median(times))
+    del work
+    torch.cuda.empty_cache()
+    if use_cache:
+        cache[key] = res
+        save_cache(cache)
+    return res
+
+
+def best_batched(sizes, d: int, **kw):
+    """(rho, reg, ms) of the fastest tile of the batched launch."""
+    res = tune_batched(sizes, d, **kw)
+    name = min(res, key=res.get)
+    rho, reg = (int(v) for v in name.split("/"))
+    return rho, reg, res[name]
 
 
 def load_cache(path: str | None = None) -> dict:

@@ -31,6 +31,34 @@ def test_autotune_small_live(tmp_path, monkeypatch):
     assert len(cache) == 3
 
 
+def test_autotune_batched_tiles(orc, tmp_path, monkeypatch):
+    # every (rho, reg) tile of the batched launch is timed; the pick is the
+    # fastest, is cached, and computes the batch correctly
+    import numpy as np
+    import torch
+    dev()
+    monkeypatch.setenv("TRI_TUNE_CACHE", str(tmp_path / "cache.json"))
+    from paper_1609_01490_gb300 import autotune, inputs, tri
+    sizes = inputs.batched_sizes(60, lo=1, hi=700, seed=12)
+    res = autotune.tune_batched(sizes, 40, reps=2)
+    assert set(res) == {f"{r}/{g}" for r, g in autotune.BATCHED_TILES} and len(res) == 11
+    rho, reg, ms = autotune.best_batched(sizes, 40, reps=2)
+    assert ms == min(res.values()) and res[f"{rho}/{reg}"] == ms
+    assert len(json.load(open(tmp_path / "cache.json"))) == 1
+    work = autotune._Batched(sizes, 40, seed=1609)
+    work.launch(rho, reg)
+    torch.cuda.synchronize()
+    x, pt_off = inputs.batched_points(np.asarray(sizes, dtype=np.uint32), 40, seed=1609)
+    o = work.out.cpu().numpy()
+    off = 0
+    for k, nk in enumerate(sizes):
+        nk = int(nk)
+        ref = orc.edm_packed(x[int(pt_off[k]): int(pt_off[k]) + nk])
+        got = o[off: off + nk * (nk + 1) // 2].astype(np.float64)
+        assert np.all(got[ref == 0] == 0) and np.all(np.abs(got - ref) <= 1e-5 * ref), k
+        off += nk * (nk + 1) // 2
+
+
 def test_selector_on_held_out_groups():
     # On the committed GB300 sweep the fixed default (lambda, rho = 16) is up to
     # a third slower than the best candidate for the Life step and the AT
