@@ -681,6 +681,60 @@ def run_split(args, rank: int, world: int, local: int):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """A few launches of one kernel on its small case, for ncu captures
+    (select the launch with -k and -s / -c): the Life step (n = 16384,
+    lambda, rho 32), the AT energy (N = 1536, table map, rho 32), the FP32
+    EDM (N = 16384, d = 64, lambda, rho 16 x 8 x 8 pairs), the batched EDM
+    (100 of the seeded instances, d = 64, rho 16 x 8 x 8) and the collision
+    test (16384 spheres in 3-D, rho 16 x 8 x 8).  Four launches each."""
+    import torch
+    from paper_1609_01490_gb300 import inputs
+    from paper_1609_01490_gb300 import tri
+    dev = torch.device("cuda")
+    case = args.profile
+    if case == "life":
+        n = 16384
+        a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)
+        b = torch.zeros_like(a)
+        for _ in range(4):
+            tri.tri_ca_step(a, b, n, map=tri.MAP_LAMBDA, rho=32)
+            a, b = b, a
+    elif case == "at":
+        p = torch.from_numpy(inputs.at_points(1536, seed=1610)).to(dev)
+        e = torch.zeros(1, dtype=torch.float64, device=dev)
+        ws = torch.empty(tri.tet_at_workspace_size(1536, 32, tri.MAP_TET_TABLE) // 8 + 1, dtype=torch.float64,
+                         device=dev)
+        for _ in range(4):
+            tri.tet_at_energy(p, e, 1.0, tri.MAP_TET_TABLE, 32, ws)
+    elif case == "edm":
+        x = torch.from_numpy(inputs.edm_normal_points(16384, 64, seed=1609)).to(dev)
+        o = torch.empty(16384 * 16385 // 2, device=dev)
+        for _ in range(4):
+            tri.tri_edm(x, o, map=tri.MAP_LAMBDA, rho=16, reg=8)
+    elif case == "batched":
+        sizes = inputs.batched_sizes(100, seed=1609)
+        xc, pt_off = inputs.batched_points(sizes, 64, seed=1609)
+        tl = sizes.astype(np.int64) * (sizes.astype(np.int64) + 1) // 2
+        oo = np.zeros(len(sizes), dtype=np.uint64)
+        oo[1:] = np.cumsum(tl)[:-1]
+        oc = torch.empty(int(tl.sum()), device=dev)
+        ws = torch.empty(tri.tri_edm_batched_workspace_size(100) // 8 + 1, dtype=torch.int64, device=dev)
+        args_b = (torch.from_numpy(xc).to(dev), torch.from_numpy(pt_off.view(np.int64)).to(dev),
+                  torch.from_numpy(sizes.astype(np.int32)).to(dev), oc, torch.from_numpy(oo.view(np.int64)).to(dev))
+        for _ in range(4):
+            tri.tri_edm_batched(*args_b, rho=16, reg=8, workspace=ws)
+    elif case == "collide":
+        c, r = inputs.spheres(16384, 3)
+        cd, rd = torch.from_numpy(c).to(dev), torch.from_numpy(r).to(dev)
+        npairs = torch.zeros(1, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(16384, dtype=torch.int32, device=dev)
+        for _ in range(4):
+            tri.tri_collide(cd, rd, npairs, count=cnt, map=tri.MAP_LAMBDA, rho=16, reg=8)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "ok": True}))
+
+
     # -------------------------------------------------------------- our arm -----
 
 
@@ -703,6 +757,8 @@ def main():
     ap.add_argument("--suite", action="store_true", help="one JSON line per other hot-path row instead")
     ap.add_argument("--only", default="", help="suite sections to run (maps,edm,life,at,collide,batched)")
     ap.add_argument("--collide-n", type=int, default=65536, help="spheres in the collision rows")
+    ap.add_argument("--profile", default="", choices=["", "life", "at", "edm", "batched", "collide"],
+                    help="run a few launches of one kernel's small case (for ncu captures) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -712,6 +768,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile:
+        run_profile_case(args)
         return
     if args.suite:
         run_suite(args)

@@ -200,7 +200,7 @@ TRI_API int tri_edm_workspace_size(uint32_t n, uint32_t d, int prec, size_t *byt
  * their own (same stream, in this order) to time them or to reuse prepared
  * operands.  workspace: tri_edm_workspace_size bytes, 256-byte aligned.
  * Tensor-core limits: n <= 92681 (packed triangle below 2^32 entries),
- * d <= 192 for BF16X6 and d <= 256 for BF16X3 (the split planes of one row
+ * d <= 192 for BF16X6 and d <= 320 for BF16X3 (the split planes of one row
  * block stay resident in shared memory beside at least two 16 KB operand
  * stages); larger sizes give TRI_ERANGE.
  *

@@ -28,9 +28,10 @@
 // of the even CTA takes the units and passes them to both CTAs' roles through
 // a small queue in shared memory (written across the pair); warp 0 of each CTA
 // issues its TMA; warps 2-17 of each CTA read TMEM back (lanes = output
-// columns), form the distances, flag cancellations and store the packed row
-// segments (P = 2: whole segments through shared memory; P = 3: one coalesced
-// 128-byte store per warp and row).  fixup: FP64 recompute of the flagged pairs.
+// columns), form the distances, flag cancellations and store the packed rows
+// (one coalesced 128-byte store per warp and row; the four warps that hold the
+// four 32-column quarters of the same rows store them together).  fixup: FP64
+// recompute of the flagged pairs.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -54,11 +55,6 @@ constexpr int NEPI = 16;                   // epilogue warps: 4 TMEM lane quarte
 constexpr int NTHREADS = 64 + 32 * NEPI;   // TMA warp, MMA warp, epilogue warps
 constexpr int EPI_ROWS = 16;               // output rows per TMEM load in the epilogue
 constexpr int NORM_FLOATS = 2 * 32;       // per epilogue warp: norms of its 32 rows of the tile (double buffered)
-constexpr int STG_ROWS = 8;                // rows staged at a time by a row group
-constexpr int STG_LD = TILE + 4;           // staging row: 128 distances shifted by the row's 16-byte phase
-constexpr int STG_FLOATS = STG_ROWS * STG_LD;  // one staging buffer
-// shared floats per row group: two staging buffers (P = 2 stages its stores)
-__host__ __device__ constexpr int group_floats(int P) { return P == 2 ? 2 * STG_FLOATS : 0; }
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 constexpr int TQ = 8;                      // unit queue slots (producer -> MMA and epilogues, both CTAs)
 constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last unit
@@ -433,9 +429,6 @@ __device__ __forceinline__ bool unit_of(uint64_t u, uint32_t mb, uint32_t &R, ui
 // pa + pb <= P - 1: hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid for P = 3
 // and hi.hi, hi.lo, lo.hi for P = 2.
 
-// Offset of packed row i0 + k within 16 bytes, T2(i0 + k) mod 4, for i0 a
-// multiple of 16 (then it equals T2(k) mod 4).
-__host__ __device__ constexpr uint32_t row_phase(uint32_t k) { return ((k * (k + 1)) >> 1) & 3u; }
 
 // Barrier among the `count` threads of one epilogue row group (ids 1..).
 __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count)
@@ -490,12 +483,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t a_bytes = (uint32_t)P * g.nkc * CHUNK_BYTES;  // this CTA's row block
     constexpr uint32_t stage_bytes = CHUNK_BYTES;               // one plane of one K chunk
-    constexpr uint32_t stg_floats = (NEPI / 4) * group_floats(P);  // store staging of the row groups
     const uint32_t sA = base;                                   // [kc][p] chunks
     const uint32_t sB = base + a_bytes;                         // [stage] chunks of one plane
     float *epi = reinterpret_cast<float *>(gbase + a_bytes + g.stages * stage_bytes);
-    float *stage_base = epi + NEPI * NORM_FLOATS;  // staging area of the row groups
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage_base + stg_floats);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(epi + NEPI * NORM_FLOATS);
     // barriers: fullA, freeA, done, tmem_full[2], tmem_empty[2], fullB[stages], emptyB[stages]
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t b_fullA = bar0, b_freeA = bar0 + 8, b_done = bar0 + 16;
@@ -802,8 +793,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         constexpr int NCH = TILE / EPI_ROWS / NG;   // 16-row chunks per warp and tile
         const uint32_t e = warp - 2, q = warp & 3, grp = e >> 2;
         float *snorm = epi + e * NORM_FLOATS;     // norms of this warp's rows, two buffers
-        float *stg = stage_base + grp * group_floats(P);  // this row group's two staging or boundary buffers
-        uint32_t hc = 0;                                   // halves staged so far (selects the buffer)
         const float tau = g.tau;
         // next tile's norms: lane l holds the norms of row l % 16 of chunks
         // u = 2v + l / 16 (16 rows each) and of its own column
@@ -904,77 +893,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                                 }
                             }
                         }
-                        if constexpr (P == 2) {
-                        // Store through shared memory in two halves of 8 rows: the row
-                        // group's four warps (one per 32-column quarter) write their
-                        // columns of each row into a staging row shifted by the row's
-                        // 16-byte phase (T2(i0 + k) mod 4, which depends on k only since
-                        // i0 is a multiple of 16); then each warp writes two whole row
-                        // segments, the aligned middle with one float4 per lane and the
-                        // ends with scalar stores, so every 128-byte line of a segment's
-                        // middle is written by one instruction.  The two staging buffers
-                        // alternate: the barrier before a half's stores also tells each
-                        // warp that the group has finished reading the buffer it will
-                        // fill next, so one barrier per half suffices.
+                        // Direct stores: for each row the warp's 32 lanes hold 32
+                        // consecutive packed entries, written by one 128-byte store.
+                        // The row group's four warps hold the four quarters of the
+                        // same 16 rows; a barrier before their stores keeps them
+                        // writing the same rows at the same time, so the partly
+                        // written 32-byte sectors at the quarters' edges meet in L2
+                        // soon after each other (BF16X6, N = 65536, d = 128: 2.24 ms
+                        // with one barrier per unit, 2.19 per tile, 2.09 per 16
+                        // rows, 2.09 per 8, 2.14 per 4).  Staging whole row segments
+                        // through shared memory competes with the tensor core's
+                        // operand reads: BF16X6 2.51 ms, BF16X3 2.42 ms against
+                        // 1.95 ms direct; assembling only the 32-byte sectors that
+                        // straddle two quarters of a row, 2.63 ms.
+                        named_sync(1 + grp, 128);
+                        float *row = g.out + T2(i0) + j;  // row i0, column j
+                        if (bi != bj && (bi + 1) * TILE <= g.n) {
 #pragma unroll
-                        for (int half = 0; half < EPI_ROWS / STG_ROWS; ++half) {
-                            float *sb = stg + (hc & 1) * STG_FLOATS;
-                            ++hc;
-#pragma unroll
-                            for (int kk = 0; kk < STG_ROWS; ++kk) {
-                                const int k = half * STG_ROWS + kk;
-                                sb[kk * STG_LD + row_phase(k) + q * 32 + lane] = dv[k];
+                            for (int k = 0; k < EPI_ROWS; ++k) {
+                                __stcs(row, dv[k]);
+                                row += i0 + k + 1;  // T2(i + 1) - T2(i)
                             }
-                            named_sync(1 + grp, 128);
-#pragma unroll
-                            for (int r2 = 0; r2 < STG_ROWS / 4; ++r2) {
-                                const uint32_t kk = q * (STG_ROWS / 4) + r2, k = half * STG_ROWS + kk, i = i0 + k;
-                                if (i < g.n) {
-                                    const uint32_t len = bi == bj ? i - bj * TILE + 1 : TILE;  // columns of row i here
-                                    float *seg = g.out + T2(i) + bj * TILE;
-                                    const uint32_t ph = row_phase(k), head = (4 - ph) & 3;
-                                    const float *src = sb + kk * STG_LD + ph;
-                                    const uint32_t h = head < len ? head : len;
-                                    const uint32_t nv = (len - h) >> 2;
-                                    if (lane < nv)
-                                        __stcs(reinterpret_cast<float4 *>(seg + h) + lane,
-                                               *reinterpret_cast<const float4 *>(src + h + 4 * lane));
-                                    const uint32_t t0 = h + 4 * nv, tail = len - t0;  // h <= 3, tail <= 3
-                                    if (lane < h) __stcs(seg + lane, src[lane]);
-                                    if (lane >= 4 && lane - 4 < tail) __stcs(seg + t0 + lane - 4, src[t0 + lane - 4]);
-                                }
-                            }
-                        }
                         } else {
-                            // Direct stores: for each row the warp's 32 lanes hold 32
-                            // consecutive packed entries, written by one 128-byte store.
-                            // For P = 3 the tensor core's operand reads already take most
-                            // of the shared-memory bandwidth: staging whole segments
-                            // (as P = 2 does) measured 2.51 ms against 2.23 ms, and
-                            // assembling only the 32-byte sectors that straddle two
-                            // quarters of a row 2.63 ms (N = 65536, d = 128, one
-                            // row-group barrier per unit).
-                            // The row group's four warps hold the four quarters of the
-                            // same 16 rows; a barrier before their stores keeps them
-                            // writing the same rows at the same time, so the partly
-                            // written 32-byte sectors at the quarters' edges meet in L2
-                            // soon after each other (2.24 ms with one barrier per unit,
-                            // 2.19 per tile, 2.09 per 16 rows, 2.09 per 8, 2.14 per 4).
-                            named_sync(1 + grp, 128);
-                            float *row = g.out + T2(i0) + j;  // row i0, column j
-                            if (bi != bj && (bi + 1) * TILE <= g.n) {
 #pragma unroll
-                                for (int k = 0; k < EPI_ROWS; ++k) {
-                                    __stcs(row, dv[k]);
-                                    row += i0 + k + 1;  // T2(i + 1) - T2(i)
-                                }
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < EPI_ROWS; ++k) {
-                                    const uint32_t i = i0 + k;
-                                    if (i < g.n && j <= i) __stcs(row, dv[k]);
-                                    row += i + 1;
-                                }
+                            for (int k = 0; k < EPI_ROWS; ++k) {
+                                const uint32_t i = i0 + k;
+                                if (i < g.n && j <= i) __stcs(row, dv[k]);
+                                row += i + 1;
                             }
                         }
                     }
@@ -1103,8 +1048,7 @@ bool plan(uint32_t d, int prec, TcPlan &p)
     p.P = prec == TRI_BF16X6 ? 3 : 2;
     p.dp = (d + KCH - 1) / KCH * KCH;
     p.nkc = p.dp / KCH;
-    const size_t stg = (size_t)(NEPI / 4) * group_floats(p.P);  // store staging (P = 2) or boundary sectors (P = 3)
-    const size_t fixed = 1024 /*align*/ + (NEPI * NORM_FLOATS + stg) * 4 + 8 * (7 + 2 * MAX_STAGES);
+    const size_t fixed = 1024 /*align*/ + NEPI * NORM_FLOATS * 4 + 8 * (7 + 2 * MAX_STAGES);
     const size_t a = (size_t)p.P * p.nkc * CHUNK_BYTES, st = CHUNK_BYTES;  // one row block per CTA
     if (fixed + a + 2 * st > (size_t)SMEM_LIMIT) return false;
     p.stages = (uint32_t)std::min<size_t>(MAX_STAGES, (SMEM_LIMIT - fixed - a) / st);

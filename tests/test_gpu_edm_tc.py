@@ -46,7 +46,7 @@ def test_tc_edm_small(orc, prec, tol, mapname):
     m = getattr(t, "MAP_" + mapname)
     cases = [(1, 3), (5, 3), (128, 64), (129, 17), (300, 128), (1000, 100), (777, 64)]
     if prec == "BF16X3":
-        cases.append((260, 256))  # four 64-wide K chunks: the BF16X3 limit
+        cases.append((260, 320))  # five 64-wide K chunks: the BF16X3 limit
     else:
         cases.append((200, 192))  # three 64-wide K chunks: the BF16X6 limit
     for n, d in cases:
@@ -278,8 +278,8 @@ def test_tc_phases_and_errors():
     with pytest.raises(t.TriError):
         t.tri_edm(x, out, map=t.MAP_RB, prec=t.BF16X6,
                   workspace=torch.empty(need, dtype=torch.uint8, device=D))
-    # d = 193 (BF16X6) and d = 257 (BF16X3) exceed the resident-operand limits
-    for dd, pr in ((193, t.BF16X6), (257, t.BF16X3)):
+    # d = 193 (BF16X6) and d = 321 (BF16X3) exceed the resident-operand limits
+    for dd, pr in ((193, t.BF16X6), (321, t.BF16X3)):
         with pytest.raises(t.TriError) as e:
             xx = torch.zeros(10, dd, device=D)
             t.tri_edm(xx, torch.empty(55, device=D), prec=pr,
