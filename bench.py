@@ -184,7 +184,7 @@ def run_reference(args, rank: int, world: int):
     total_pairs = N_PTS * (N_PTS + 1) // 2
     vals, secs = [], []
     for s in range(args.warmup + args.steps):
-        rate, thr, sample, dt = cpu_oracle_sample(x, target_s=8.0, with_time=True)
+        rate, thr, sample, dt = cpu_oracle_sample(x, target_s=4.0, with_time=True)
         if s >= args.warmup:
             vals.append(rate)
             secs.append(dt)
@@ -235,11 +235,13 @@ def graph_time_ms(fn, reps, stream):
 
 
 def paper_comparison(tri, inputs, dev, stream):
-    """The paper's own comparison (Section 5) on this GPU, beside the headline:
-    the paper-size EDM (N = 2048, d = 3, one pair per thread, rho = 16, as the
-    paper launches it) and one triangular Life step at n = 16384 (rho = 32),
-    under lambda, the bounding box and the rectangular box.  Each time is the
-    mean of many launches captured in one CUDA graph; I = t_BB / t_map."""
+    """The other workloads beside the headline, each timed on this GPU as the
+    mean of launches captured in one CUDA graph: the paper's own comparison
+    (Section 5) of lambda, the bounding box and the rectangular box on the
+    paper-size EDM (N = 2048, d = 3, one pair per thread, rho = 16, as the
+    paper launches it) and on one triangular Life step (n = 16384, rho = 32);
+    the Axilrod-Teller energy under the tetrahedral maps; and the 1000-instance
+    batched EDM against separate launches.  I = t_BB / t_map."""
     import torch
     out = {}
     x = torch.from_numpy(inputs.edm_uniform_points(2048, 3, seed=1609)).to(dev)
@@ -261,6 +263,45 @@ def paper_comparison(tri, inputs, dev, stream):
          for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB))}
     out["life_n16384_step_rho32"] = {"ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()}}
     del x, o, a, b
+    # the Axilrod-Teller energy over the tetrahedral domain (Section 6), N = 1536, rho = 32:
+    # the cubic-root map, the table of layer starts (Section 7) and the m^3 box
+    pts = torch.from_numpy(inputs.at_points(1536, seed=1610)).to(dev)
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    ws = torch.empty(tri.tet_at_workspace_size(1536, 32, tri.MAP_BB) // 8 + 1, dtype=torch.float64, device=dev)
+    t = {nm: graph_time_ms(lambda: tri.tet_at_energy(pts, e, 1.0, m, 32, ws), 20, stream)
+         for nm, m in (("lambda", tri.MAP_LAMBDA), ("lambda_table", tri.MAP_TET_TABLE), ("bb", tri.MAP_BB))}
+    out["at_energy_n1536_rho32"] = {"ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()}}
+    del pts, e, ws
+    # 1000 uneven EDM triangles (N log-uniform in [64, 8192], d = 64): one
+    # persistent launch at the autotuner's tile against 1000 separate lambda
+    # launches, each captured in a CUDA graph
+    from paper_1609_01490_gb300 import autotune
+    sizes = inputs.batched_sizes(1000, seed=1609)
+    xc, pt_off = inputs.batched_points(sizes, 64, seed=1609)
+    tl = sizes.astype(np.int64) * (sizes.astype(np.int64) + 1) // 2
+    oo = np.zeros(len(sizes), dtype=np.uint64)
+    oo[1:] = np.cumsum(tl)[:-1]
+    xd = torch.from_numpy(xc).to(dev)
+    oc = torch.empty(int(tl.sum()), dtype=torch.float32, device=dev)
+    pto = torch.from_numpy(pt_off.view(np.int64)).to(dev)
+    nk = torch.from_numpy(sizes.astype(np.int32)).to(dev)
+    ood = torch.from_numpy(oo.view(np.int64)).to(dev)
+    wsb = torch.empty(tri.tri_edm_batched_workspace_size(1000) // 8 + 1, dtype=torch.int64, device=dev)
+    rho_b, reg_b, _ = autotune.best_batched(sizes, 64, reps=3)
+    t_b = graph_time_ms(lambda: tri.tri_edm_batched(xd, pto, nk, oc, ood, rho=rho_b, reg=reg_b, workspace=wsb), 1,
+                        stream)
+    views = [(xd[int(pt_off[k]): int(pt_off[k]) + int(sizes[k])], oc[int(oo[k]): int(oo[k]) + int(tl[k])])
+             for k in range(1000)]
+
+    def separate():
+        for xv, ov in views:
+            tri.tri_edm(xv, ov, map=tri.MAP_LAMBDA, rho=16, reg=0)
+    t_s = graph_time_ms(separate, 1, stream)
+    out["edm_batched_1000_d64"] = {"ms": {"persistent": t_b, "separate_1000_launches": t_s},
+                                   "tile": {"rho": rho_b, "reg": reg_b}, "pairs": int(tl.sum()),
+                                   "speedup_over_separate": t_s / t_b}
+    del xd, oc, views
+    torch.cuda.empty_cache()
     return out
 
 

@@ -103,10 +103,13 @@ __global__ void __launch_bounds__(4 * RHO) ca_kernel(const uint8_t *__restrict__
 }
 
 // Conway's rule bit-sliced: one bit per cell, 32 cells per word.  Tile S x S,
-// S = 4*RHO, with S/2 threads: thread t takes the 32-cell strip c = t % NS
-// (NS = S/32) of the tile rows [HR g, HR g + HR), g = t / NS, HR = S/16, and
-// reads its HR + 2 input rows (one above, one below) as two 16-byte loads
-// each.  Each row's 32 bytes become one word (bit b = byte b non-zero,
+// S = 4*RHO, with NS (S / HR) threads: thread t takes the 32-cell strip c =
+// t % NS (NS = S/32) of the tile rows [HR g, HR g + HR), g = t / NS, HR =
+// min(S/16, 4), and reads its HR + 2 input rows (one above, one below) as two
+// 16-byte loads each, all issued before any is used.  (At S = 128 four rows
+// per thread in 128-thread blocks took 0.0633 ms per step at n = 16384
+// against 0.0657 ms for eight rows in 64-thread blocks; the bounding box gave
+// 0.0764 and 0.0612 ms.)  Each row's 32 bytes become one word (bit b = byte b non-zero,
 // cleared past the diagonal and outside rows [0, n)); the cells left and
 // right of the strip come from the neighbouring lanes' words by shuffle, or,
 // at the tile's edges, from a 4-byte load beyond it.  Per row, the three
@@ -128,12 +131,18 @@ __device__ __forceinline__ uint32_t nibble_bytes(uint32_t nib)  // bit b -> byte
 
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (a & c) | (b & c); }
 
+// rows per thread and threads per block of the bit-sliced step
+template <int RHO>
+__host__ __device__ constexpr int life_rows() { return (4 * RHO) / 16 < 4 ? (4 * RHO) / 16 : 4; }
+template <int RHO>
+__host__ __device__ constexpr int life_threads() { return (4 * RHO / 32) * (4 * RHO / life_rows<RHO>()); }
+
 template <int MAP, int RHO>
-__global__ void __launch_bounds__(2 * RHO) ca_life_bits_kernel(const uint8_t *__restrict__ in,
-                                                               uint8_t *__restrict__ out, uint32_t n, size_t ld,
-                                                               BlockMap bm)
+__global__ void __launch_bounds__(life_threads<RHO>()) ca_life_bits_kernel(const uint8_t *__restrict__ in,
+                                                                            uint8_t *__restrict__ out, uint32_t n,
+                                                                            size_t ld, BlockMap bm)
 {
-    constexpr int S = 4 * RHO, NT = S / 2, NS = S / 32, HR = S / 16;
+    constexpr int S = 4 * RHO, NS = S / 32, HR = life_rows<RHO>(), NT = NS * (S / HR);
     constexpr unsigned FULL = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
     uint32_t bi, bj;
     if (!map_block<MAP>(bm, bi, bj)) return;
@@ -141,26 +150,33 @@ __global__ void __launch_bounds__(2 * RHO) ca_life_bits_kernel(const uint8_t *__
     const long long cc = (long long)bj * S + 32 * c;      // first cell (byte) column of the strip
     const long long a0 = (long long)bi * S + HR * g - 1;  // global row of the first register row
     uint32_t B[HR + 2], sH[HR + 2], cH[HR + 2];
+    // all of the strip's loads first (2 x 16 bytes per row and the edge
+    // words), so that they are in flight together; then the bit packing
+    uint4 v0[HR + 2], v1[HR + 2];
+    uint32_t le[HR + 2], re[HR + 2];
 #pragma unroll
     for (int q = 0; q < HR + 2; ++q) {
         const long long a = a0 + q;
         const bool rok = a >= 0 && a < (long long)n;
         const uint8_t *row = in + (rok ? (size_t)a * ld : 0);
-        uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
-        if (rok && cc <= a) v0 = __ldg(reinterpret_cast<const uint4 *>(row + cc));
-        if (rok && cc + 16 <= a) v1 = __ldg(reinterpret_cast<const uint4 *>(row + cc + 16));
-        uint32_t b = alive_nibble(v0.x) | (alive_nibble(v0.y) << 4) | (alive_nibble(v0.z) << 8) |
-                     (alive_nibble(v0.w) << 12) | (alive_nibble(v1.x) << 16) | (alive_nibble(v1.y) << 20) |
-                     (alive_nibble(v1.z) << 24) | (alive_nibble(v1.w) << 28);
+        v0[q] = v1[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (rok && cc <= a) v0[q] = __ldg(reinterpret_cast<const uint4 *>(row + cc));
+        if (rok && cc + 16 <= a) v1[q] = __ldg(reinterpret_cast<const uint4 *>(row + cc + 16));
+        le[q] = (c == 0 && rok && cc >= 4 && cc - 1 <= a) ? __ldg(reinterpret_cast<const uint32_t *>(row + cc - 4)) : 0u;
+        re[q] = (c == NS - 1 && rok && cc + 32 <= a) ? __ldg(reinterpret_cast<const uint32_t *>(row + cc + 32)) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < HR + 2; ++q) {
+        const long long a = a0 + q;
+        const bool rok = a >= 0 && a < (long long)n;
+        uint32_t b = alive_nibble(v0[q].x) | (alive_nibble(v0[q].y) << 4) | (alive_nibble(v0[q].z) << 8) |
+                     (alive_nibble(v0[q].w) << 12) | (alive_nibble(v1[q].x) << 16) | (alive_nibble(v1[q].y) << 20) |
+                     (alive_nibble(v1[q].z) << 24) | (alive_nibble(v1[q].w) << 28);
         const long long inside = a - cc;  // columns cc .. cc + inside lie in the domain
         b = !rok || inside < 0 ? 0u : (inside >= 31 ? b : b & ((2u << inside) - 1u));
         B[q] = b;
         // the cells beyond the strip's ends
-        uint32_t lb = 0u, rb = 0u;
-        if (c == 0 && rok && cc >= 4 && cc - 1 <= a)
-            lb = __ldg(reinterpret_cast<const uint32_t *>(row + cc - 4)) >> 24 ? 1u : 0u;
-        if (c == NS - 1 && rok && cc + 32 <= a)
-            rb = __ldg(reinterpret_cast<const uint32_t *>(row + cc + 32)) & 0xFFu ? 1u : 0u;
+        uint32_t lb = le[q] >> 24 ? 1u : 0u, rb = re[q] & 0xFFu ? 1u : 0u;
         const uint32_t up = __shfl_up_sync(FULL, b, 1, NS);    // strip c - 1
         const uint32_t dn = __shfl_down_sync(FULL, b, 1, NS);  // strip c + 1
         if (c > 0) lb = up >> 31;
@@ -199,9 +215,9 @@ void launch_rule(uint32_t rho, dim3 g, cudaStream_t s, const uint8_t *in, uint8_
 {
     if constexpr (LIFE) {
         switch (rho) {
-        case 8: ca_life_bits_kernel<MAP, 8><<<g, 16, 0, s>>>(in, out, n, ld, bm); return;
-        case 16: ca_life_bits_kernel<MAP, 16><<<g, 32, 0, s>>>(in, out, n, ld, bm); return;
-        default: ca_life_bits_kernel<MAP, 32><<<g, 64, 0, s>>>(in, out, n, ld, bm); return;
+        case 8: ca_life_bits_kernel<MAP, 8><<<g, life_threads<8>(), 0, s>>>(in, out, n, ld, bm); return;
+        case 16: ca_life_bits_kernel<MAP, 16><<<g, life_threads<16>(), 0, s>>>(in, out, n, ld, bm); return;
+        default: ca_life_bits_kernel<MAP, 32><<<g, life_threads<32>(), 0, s>>>(in, out, n, ld, bm); return;
         }
     }
     switch (rho) {
