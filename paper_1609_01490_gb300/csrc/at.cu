@@ -11,13 +11,18 @@ using namespace tri;
 
 namespace {
 
-// Block (L, R, C), L >= R >= C, of rho x rho threads: thread (ty, tx) takes
-// i = L*rho + ty and j = R*rho + tx and loops k over block C (k < j).  With
-// squared sides a = |ij|^2, b = |jk|^2, c = |ki|^2 the law of cosines gives
-// cos g_i cos g_j cos g_k = (a+c-b)(a+b-c)(b+c-a) / (8abc) and
+// Block (L, R, C), L >= R >= C, of rho x (rho / AT_ROWS) threads: thread
+// (ty, tx) takes j = R*rho + tx and the AT_ROWS rows i = L*rho + ty + u*(rho /
+// AT_ROWS), and loops k over block C (k < j), each b(j, k) read once for all
+// its rows.  With squared sides a = |ij|^2, b = |jk|^2, c = |ki|^2 the law of
+// cosines gives cos g_i cos g_j cos g_k = (a+c-b)(a+b-c)(b+c-a) / (8abc) and
 // (r_ij r_jk r_ki)^3 = (abc)^(3/2).  Terms are formed and summed per thread in
-// FP32 (two k at a time with f32x2 instructions, into two running sums), summed
-// over each warp in FP32 and over the warps in FP64 into partial[T3(L)+T2(R)+C].
+// FP32 (two k at a time with f32x2 instructions, into two running sums per
+// row), summed over each warp in FP32 and over the warps in FP64 into
+// partial[T3(L)+T2(R)+C].  (Two rows per thread halve the per-triplet share
+// of the block's setup: the map, the pair quantities and the sums.)
+constexpr int AT_ROWS = 2;
+
 template <int MAP>
 __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, uint32_t m, uint64_t nblocks,
                           double *__restrict__ partial)
@@ -40,12 +45,14 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
     // padded by two floats so that a warp's 8-byte loads of (k, k + 1) fall on
     // distinct banks.
     __shared__ __align__(8) float sb[32][34], sc[32][34];
-    __shared__ double wsum[32];
-    const uint32_t rho = blockDim.x;
+    __shared__ double wsum[16];
+    const uint32_t rho = blockDim.x, rows = blockDim.y;  // rows = rho / AT_ROWS
     const uint32_t tid = threadIdx.y * rho + threadIdx.x;
-    {
-        const uint32_t kk = C * rho + threadIdx.x;
-        const uint32_t jj = R * rho + threadIdx.y, ii = L * rho + threadIdx.y;
+    const uint32_t kk = C * rho + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < AT_ROWS; ++u) {
+        const uint32_t r = threadIdx.y + u * rows;
+        const uint32_t jj = R * rho + r, ii = L * rho + r;
         float bv = 0.0f, cv = 0.0f;
         if (kk < n) {
             const float xk = p[3 * kk], yk = p[3 * kk + 1], zk = p[3 * kk + 2];
@@ -58,49 +65,74 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
                 cv = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
             }
         }
-        sb[threadIdx.y][threadIdx.x] = bv;
-        sc[threadIdx.y][threadIdx.x] = cv;
+        sb[r][threadIdx.x] = bv;
+        sc[r][threadIdx.x] = cv;
     }
     __syncthreads();
-    const uint32_t i = L * rho + threadIdx.y, j = R * rho + threadIdx.x;
+    const uint32_t j = R * rho + threadIdx.x;
     float s = 0.0f;
-    if (i < n && j < i) {
-        const float xi = p[3 * i], yi = p[3 * i + 1], zi = p[3 * i + 2];
+    if (j < n) {
         const float xj = p[3 * j], yj = p[3 * j + 1], zj = p[3 * j + 2];
-        const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
-        const float a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        // row u takes part iff j < i_u < n; a row that does not is computed
+        // on a dummy side (a = 1) and left out of the sum
+        bool act[AT_ROWS];
+        f2 A[AT_ROWS], S[AT_ROWS];
+        float a1[AT_ROWS];
+        const float *crow[AT_ROWS];
+#pragma unroll
+        for (int u = 0; u < AT_ROWS; ++u) {
+            const uint32_t r = threadIdx.y + u * rows, i = L * rho + r;
+            act[u] = i < n && j < i;
+            float a = 1.0f;
+            if (act[u]) {
+                const float dx = p[3 * i] - xj, dy = p[3 * i + 1] - yj, dz = p[3 * i + 2] - zj;
+                a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            }
+            a1[u] = a;
+            A[u] = f2_pack(a, a);
+            S[u] = f2_pack(0.0f, 0.0f);
+            crow[u] = sc[r];
+        }
         const uint32_t kend = min(j, (C + 1) * rho) - C * rho;  // k < j
-        const float *brow = sb[threadIdx.x], *crow = sc[threadIdx.y];
-        const f2 A = f2_pack(a, a), K = f2_pack(0.375f, 0.375f), ONE = f2_pack(1.0f, 1.0f);
-        f2 S = f2_pack(0.0f, 0.0f);
+        const float *brow = sb[threadIdx.x];
+        const f2 K = f2_pack(0.375f, 0.375f), ONE = f2_pack(1.0f, 1.0f);
         uint32_t t = 0;
         for (; t + 1 < kend; t += 2) {
-            const f2 b = *reinterpret_cast<const f2 *>(&brow[t]), c = *reinterpret_cast<const f2 *>(&crow[t]);
-            const f2 q = f2_mul(f2_mul(A, b), c);
-            const f2 P = f2_mul(f2_mul(f2_sub(f2_add(A, c), b), f2_sub(f2_add(A, b), c)), f2_sub(f2_add(b, c), A));
-            float q0, q1;
-            f2_unpack(q, q0, q1);
-            const f2 rs = f2_pack(rsqrtf(q0), rsqrtf(q1));
-            const f2 inv = f2_mul(rs, rs);
-            S = f2_add(S, f2_mul(f2_mul(f2_fma(f2_mul(K, P), inv, ONE), inv), rs));
+            const f2 b = *reinterpret_cast<const f2 *>(&brow[t]);
+#pragma unroll
+            for (int u = 0; u < AT_ROWS; ++u) {
+                const f2 c = *reinterpret_cast<const f2 *>(&crow[u][t]);
+                const f2 q = f2_mul(f2_mul(A[u], b), c);
+                const f2 P = f2_mul(f2_mul(f2_sub(f2_add(A[u], c), b), f2_sub(f2_add(A[u], b), c)),
+                                    f2_sub(f2_add(b, c), A[u]));
+                float q0, q1;
+                f2_unpack(q, q0, q1);
+                const f2 rs = f2_pack(rsqrtf(q0), rsqrtf(q1));
+                const f2 inv = f2_mul(rs, rs);
+                S[u] = f2_add(S[u], f2_mul(f2_mul(f2_fma(f2_mul(K, P), inv, ONE), inv), rs));
+            }
         }
-        float s0, s1;
-        f2_unpack(S, s0, s1);
-        s = s0 + s1;
-        for (; t < kend; ++t) {
-            const float b = brow[t], c = crow[t];
-            const float q = a * b * c;
-            const float P = (a + c - b) * (a + b - c) * (b + c - a);
-            const float rs = rsqrtf(q);
-            const float inv = rs * rs;
-            s += fmaf(0.375f * P, inv, 1.0f) * inv * rs;
+#pragma unroll
+        for (int u = 0; u < AT_ROWS; ++u) {
+            float s0, s1;
+            f2_unpack(S[u], s0, s1);
+            float su = s0 + s1;
+            if (t < kend) {  // an odd last k
+                const float a = a1[u], b = brow[t], c = crow[u][t];
+                const float q = a * b * c;
+                const float P = (a + c - b) * (a + b - c) * (b + c - a);
+                const float rs = rsqrtf(q);
+                const float inv = rs * rs;
+                su += fmaf(0.375f * P, inv, 1.0f) * inv * rs;
+            }
+            if (act[u]) s += su;
         }
     }
     // warp sums in FP32 (5 more roundings of at most 2^-24 of the magnitude
     // sum each; FP64 arithmetic is scarce on this part), warp totals in FP64
     float v = s;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const uint32_t nthreads = rho * rho, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nthreads = rho * rows, lane = tid & 31, warp = tid >> 5;
     if (lane == 0) wsum[warp] = (double)v;
     __syncthreads();
     if (tid == 0) {
@@ -147,7 +179,7 @@ static int at_energy_launch(const float *xyz, uint32_t n, double nu, double *ene
 {
     const uint64_t m = ((uint64_t)n + rho - 1) / rho;
     const uint64_t nb = T3(m);
-    const dim3 blk(rho, rho);
+    const dim3 blk(rho, rho / AT_ROWS);
     if (map == TRI_MAP_LAMBDA || map == TRI_MAP_TET_TABLE) {
         if (nb > 0xFFFFFFFFull) return TRI_ERANGE;
         if (map == TRI_MAP_LAMBDA)
