@@ -55,6 +55,9 @@ constexpr int NEPI = 16;                   // epilogue warps: 4 TMEM lane quarte
 constexpr int NTHREADS = 64 + 32 * NEPI;   // TMA warp, MMA warp, epilogue warps
 constexpr int EPI_ROWS = 16;               // output rows per TMEM load in the epilogue
 constexpr int NORM_FLOATS = 2 * 32;       // per epilogue warp: norms of its 32 rows of the tile (double buffered)
+// Each epilogue warp holds TILE / (NEPI / 4) rows of a tile: the norm buffers
+// and the prefetch pattern are sized for 32 (16 epilogue warps).
+static_assert(TILE / (NEPI / 4) == 32, "epilogue norm buffers assume 32 rows per warp and tile");
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 constexpr int TQ = 8;                      // unit queue slots (producer -> MMA and epilogues, both CTAs)
 constexpr unsigned long long TQ_END = ~0ull;  // queue entry after the last unit
