@@ -4,6 +4,8 @@
 // automaton that Section 1 lists among the TD problems).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "tri_maps.cuh"
 
 using namespace tri;
@@ -137,12 +139,38 @@ __host__ __device__ constexpr int life_rows() { return (4 * RHO) / 16 < 4 ? (4 *
 template <int RHO>
 __host__ __device__ constexpr int life_threads() { return (4 * RHO / 32) * (4 * RHO / life_rows<RHO>()); }
 
+// The step is bound by the latency of its loads.  With 128 x 128-cell tiles
+// (rho = 32) each block therefore first asks L2 to prefetch the input rows of
+// the tile whose block starts `ahead` grid positions later (half the blocks
+// resident at once): by the time that block runs, its rows are on their way
+// from DRAM or in L2.  At n = 16384 this took lambda from 0.0624 to 0.0555 ms
+// per step and the bounding box from 0.0754 to 0.0650 ms (a fixed 512
+// positions: 0.0548; 1024: 0.0602; 2048: 0.0746).  With 64 x 64-cell tiles
+// (one-warp blocks) the prefetches cost more than they save (0.0739 ->
+// 0.0829 ms), so ahead = 0 there.
 template <int MAP, int RHO>
 __global__ void __launch_bounds__(life_threads<RHO>()) ca_life_bits_kernel(const uint8_t *__restrict__ in,
                                                                             uint8_t *__restrict__ out, uint32_t n,
-                                                                            size_t ld, BlockMap bm)
+                                                                            size_t ld, BlockMap bm, uint32_t ahead)
 {
     constexpr int S = 4 * RHO, NS = S / 32, HR = life_rows<RHO>(), NT = NS * (S / HR);
+    if (ahead) {
+        uint32_t pi, pj;
+        if (map_block_ahead<MAP>(bm, ahead, pi, pj)) {
+            // two 128-byte lines per input row of that tile (rows outside the
+            // grid or wholly above the diagonal are skipped; the second line
+            // only when it lies inside the row)
+            const long long c0 = (long long)pj * S;
+            for (int r = threadIdx.x; r < S + 2; r += NT) {
+                const long long a = (long long)pi * S + r - 1;
+                if (a >= 0 && a < (long long)n && c0 <= a) {
+                    const uint8_t *q = in + (size_t)a * ld + (size_t)c0;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+                    if ((size_t)c0 + 127 < ld) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + 127));
+                }
+            }
+        }
+    }
     constexpr unsigned FULL = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
     uint32_t bi, bj;
     if (!map_block<MAP>(bm, bi, bj)) return;
@@ -209,15 +237,40 @@ __global__ void __launch_bounds__(life_threads<RHO>()) ca_life_bits_kernel(const
     }
 }
 
+// Half the blocks of this kernel that fit on the GPU at once (the L2
+// prefetch distance of the Life step), looked up once per device.
+template <int MAP, int RHO>
+uint32_t life_ahead()
+{
+    static std::mutex mu;
+    static int cached_dev = -1;
+    static uint32_t cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev != cached_dev) {
+        int per = 0, nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ca_life_bits_kernel<MAP, RHO>, life_threads<RHO>(), 0) !=
+            cudaSuccess)
+            per = 0;
+        cached = (uint32_t)(nsm > 0 && per > 0 ? nsm * per / 2 : 0);
+        cached_dev = dev;
+    }
+    return cached;
+}
+
 template <int MAP, bool LIFE>
 void launch_rule(uint32_t rho, dim3 g, cudaStream_t s, const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
                  uint32_t table, BlockMap bm)
 {
     if constexpr (LIFE) {
         switch (rho) {
-        case 8: ca_life_bits_kernel<MAP, 8><<<g, life_threads<8>(), 0, s>>>(in, out, n, ld, bm); return;
-        case 16: ca_life_bits_kernel<MAP, 16><<<g, life_threads<16>(), 0, s>>>(in, out, n, ld, bm); return;
-        default: ca_life_bits_kernel<MAP, 32><<<g, life_threads<32>(), 0, s>>>(in, out, n, ld, bm); return;
+        case 8: ca_life_bits_kernel<MAP, 8><<<g, life_threads<8>(), 0, s>>>(in, out, n, ld, bm, 0u); return;
+        case 16: ca_life_bits_kernel<MAP, 16><<<g, life_threads<16>(), 0, s>>>(in, out, n, ld, bm, 0u); return;
+        default:
+            ca_life_bits_kernel<MAP, 32><<<g, life_threads<32>(), 0, s>>>(in, out, n, ld, bm, life_ahead<MAP, 32>());
+            return;
         }
     }
     switch (rho) {

@@ -109,12 +109,17 @@ enum : int {
     MAP_LAMBDA_ND = 100  // strict lambda (Eq. eq_theorem_nodiag), shifted by one row
 };
 
+// The block of grid position (bx, by) in a grid of gx columns: map_block
+// for the running block, and for any other position of the same launch (a
+// kernel may prefetch for the block that will run a given number of
+// positions later).
 template <int MAP, int SQ = TRI_SQRT_R>
-__device__ __forceinline__ bool map_block(const BlockMap &a, uint32_t &bi, uint32_t &bj)
+__device__ __forceinline__ bool map_block_at(const BlockMap &a, uint32_t bx, uint32_t by, uint32_t gx, uint32_t &bi,
+                                             uint32_t &bj)
 {
     if constexpr (MAP == MAP_LAMBDA || MAP == MAP_LAMBDA_PD || MAP == MAP_LAMBDA_ND) {
         // omega from the (1-D, 2-D or P_Delta) grid, row-major over the grid
-        const uint64_t w = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        const uint64_t w = (uint64_t)by * gx + bx;
         if (w >= a.nblocks) return false;
         if constexpr (MAP == MAP_LAMBDA_ND) {
             uint32_t I;
@@ -126,14 +131,14 @@ __device__ __forceinline__ bool map_block(const BlockMap &a, uint32_t &bi, uint3
         return true;
     } else if constexpr (MAP == MAP_BB) {
         // Section 4.2: the m x m box; blocks above the diagonal leave at once
-        bi = blockIdx.y;
-        bj = blockIdx.x;
+        bi = by;
+        bj = bx;
         return bj <= bi;
     } else if constexpr (MAP == MAP_RB) {
         // Section 4.2, rectangular box: the part of the box right of the
         // diagonal is rotated under it.  Grid: m columns x h rows, h =
         // (m+1)/2 for odd m, m/2 + 1 for even m (whose last row is half used).
-        const uint32_t tx = blockIdx.x, ty = blockIdx.y, m = a.m;
+        const uint32_t tx = bx, ty = by, m = a.m;
         if (tx < ty) {
             bi = ty - 1;
             bj = tx;
@@ -149,17 +154,34 @@ __device__ __forceinline__ bool map_block(const BlockMap &a, uint32_t &bi, uint3
         // side s = 2^(l-1) blocks, square q covering block rows
         // [q 2^l + s, (q+1) 2^l) and block columns [q 2^l, q 2^l + s).
         if (a.level == 0) {
-            bi = bj = blockIdx.x;
+            bi = bj = bx;
         } else {
             const uint32_t s = 1u << (a.level - 1);
-            const uint32_t q = blockIdx.y >> (a.level - 1), r = blockIdx.y & (s - 1);
+            const uint32_t q = by >> (a.level - 1), r = by & (s - 1);
             bi = (q << a.level) + s + r;
-            bj = (q << a.level) + blockIdx.x;
+            bj = (q << a.level) + bx;
         }
         return true;
     } else {
         return false;
     }
+}
+
+template <int MAP, int SQ = TRI_SQRT_R>
+__device__ __forceinline__ bool map_block(const BlockMap &a, uint32_t &bi, uint32_t &bj)
+{
+    return map_block_at<MAP, SQ>(a, blockIdx.x, blockIdx.y, gridDim.x, bi, bj);
+}
+
+// The block `ahead` grid positions after the running one (row-major over the
+// grid), if that position exists and maps to a block.
+template <int MAP, int SQ = TRI_SQRT_R>
+__device__ __forceinline__ bool map_block_ahead(const BlockMap &a, uint32_t ahead, uint32_t &bi, uint32_t &bj)
+{
+    const uint64_t lin = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x + ahead;
+    const uint64_t y = lin / gridDim.x;
+    if (y >= gridDim.y) return false;
+    return map_block_at<MAP, SQ>(a, (uint32_t)(lin - y * gridDim.x), (uint32_t)y, gridDim.x, bi, bj);
 }
 
 // --------------------------------------------------------------- UTM ----

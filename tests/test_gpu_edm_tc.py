@@ -141,6 +141,61 @@ def test_tc_edm_full_size_sampled(orc):
         assert int(nf.item()) >= len(dup)
 
 
+def test_edm_largest_triangle(orc):
+    # n = 92681, the largest n whose packed triangle stays below 2^32 entries
+    # (4,294,930,221 distances, 17.2 GB): the tensor-core path (BF16X6) and
+    # the FP32 path (lambda, 4 x 4 pairs per thread) on sampled pairs, whole
+    # blocks at the first rows, the diagonal and the far corner, the pairs
+    # around packed offsets 2^31 and 2^32 - 1, every duplicated pair, and
+    # guard words past the end
+    import torch
+    t = tri()
+    n, d = 92681, 64
+    size = n * (n + 1) // 2
+    assert size < 1 << 32 and (n + 1) * (n + 2) // 2 >= 1 << 32
+    x = inputs.edm_normal_points(n, d, seed=92681, dup_frac=0.001)
+    D = dev()
+    xd = torch.from_numpy(x).to(D)
+    rng = np.random.default_rng(7)
+    pi = rng.integers(0, n, 200_000)
+    pj = (rng.random(200_000) * (pi + 1)).astype(np.int64)
+    ti, tj = np.tril_indices(300)
+    last = np.arange(n - 300, n)
+    ci, cj = np.repeat(last, 512), np.tile(np.arange(512), 300)   # far corner: the last 300 rows, columns 0..511
+    di, dj = np.repeat(last, 300), (last[:, None] - np.arange(300)[None, :]).ravel()  # last rows at the diagonal
+    # the packed offsets around 2^31 and the end of the triangle
+    extra = []
+    for w0 in (1 << 31, size - 1):
+        for w in range(w0 - 600, w0 + 600):
+            if 0 <= w < size:
+                i = (int(np.sqrt(8 * w + 1)) - 1) // 2
+                while i * (i + 1) // 2 > w:
+                    i -= 1
+                while (i + 1) * (i + 2) // 2 <= w:
+                    i += 1
+                extra.append((i, w - i * (i + 1) // 2))
+    ei, ej = np.array(extra, dtype=np.int64).T
+    dup = inputs.duplicate_pairs(x)
+    pi = np.concatenate([pi, ti, ci, di, ei, dup[:, 0]])
+    pj = np.concatenate([pj, tj, cj, dj, ej, dup[:, 1]])
+    ref = orc.edm_pairs(x, pi, pj)
+    idx = torch.from_numpy(pi * (pi + 1) // 2 + pj).to(D)
+    out = torch.full((size + 64,), -7.0, dtype=torch.float32, device=D)
+    ws = torch.empty(t.tri_edm_workspace_size(n, d, t.BF16X6), dtype=torch.uint8, device=D)
+    nf = torch.zeros(1, dtype=torch.int64, device=D)
+    t.tri_edm(xd, out, map=t.MAP_LAMBDA, prec=t.BF16X6, workspace=ws, n_flagged=nf)
+    torch.cuda.synchronize()
+    assert int(ws[8:12].view(torch.int32).item()) == 0
+    assert torch.all(out[size:] == -7.0)
+    assert rel_err(out[idx].cpu().numpy(), ref) <= 1e-5
+    assert int(nf.item()) >= len(dup)
+    out[:size].fill_(-1.0)
+    t.tri_edm(xd, out, map=t.MAP_LAMBDA, rho=16, reg=4, prec=t.FP32)
+    torch.cuda.synchronize()
+    assert torch.all(out[size:] == -7.0)
+    assert rel_err(out[idx].cpu().numpy(), ref) <= 1e-5
+
+
 def _full_compare(orc, x, outs, bands=16):
     """Every pair of the packed triangle of each host array in `outs` against
     the FP64 oracle, in row bands of equal pair count.  Returns, per array,
