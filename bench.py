@@ -65,26 +65,37 @@ def host_cores() -> int:
 
 # ----------------------------------------------------------- clocks --------
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 20 ms, with timestamps) around the timed
+    region; the summary keeps the samples that fall inside it (mark_begin /
+    mark_end), and says how many there were."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.begin = self.end = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.INTERVAL_MS)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
+
+    def mark_begin(self):
+        self.begin = _now()
+
+    def mark_end(self):
+        self.end = _now()
 
     def stop(self):
         if self.proc is not None:
@@ -93,30 +104,54 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
-            for line in open(self.path):
-                f = [x.strip() for x in line.split(",")]
-                if len(f) < 9:
-                    continue
-                try:
-                    sm.append(float(f[1]))
-                    smax.append(float(f[2]))
-                except ValueError:
-                    continue
-                for nm, v in zip(names, f[5:9]):
-                    if v.lower() in ("active", "1", "yes"):
-                        reasons.add(nm)
+            with open(self.path) as f:
+                lines = f.readlines()
         except OSError:
-            pass
+            lines = []
         finally:
             try:
                 os.unlink(self.path)
             except OSError:
                 pass
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return self.summarize(lines, self.begin, self.end)
+
+    @classmethod
+    def summarize(cls, lines, begin=None, end=None):
+        """Median SM clock, maximum clock and active throttle reasons of the
+        samples within [begin, end] (widened by one interval on each side),
+        or of all samples when none fall inside."""
+        import datetime
+        rows = []
+        for line in lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm, smax = float(f[2]), float(f[3])
+            except ValueError:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                ts = None  # an unexpected timestamp format: the sample counts only in the overall summary
+            rs = {nm for nm, v in zip(cls.REASONS, f[6:10]) if v.lower() in ("active", "1", "yes")}
+            rows.append((ts, sm, smax, rs))
+        inside = rows
+        if begin is not None and end is not None:
+            pad = datetime.timedelta(milliseconds=cls.INTERVAL_MS)
+            inside = [r for r in rows if r[0] is not None and begin - pad <= r[0] <= end + pad]
+        use = inside if inside else rows
+        return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": sorted(set().union(*[r[3] for r in use])) if use else [],
+                "samples": len(rows), "samples_in_timed_region": len(inside),
+                "interval_ms": cls.INTERVAL_MS}
+
+
+def _now():
+    import datetime
+    return datetime.datetime.now()
 
 
 # ------------------------------------------------------ reference arm -------
@@ -675,25 +710,29 @@ def run_split(args, rank: int, world: int, local: int):
     def step():
         tri.tri_edm_rows(x, rb, re_, band, map=tri.MAP_LAMBDA, prec=prec, workspace=ws)
 
-    def timed(fn, k, w):
+    def timed(fn, k, w, sampler=None):
         for _ in range(w):
             fn()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark_begin()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark_end()
         if world > 1:
             dist.barrier()
         return e0.elapsed_time(e1) / k
 
     sampler = ClockSampler(local)
     sampler.start()
-    ms = max_over_ranks([timed(step, args.steps, args.warmup)], world, dev)[0]
+    ms = max_over_ranks([timed(step, args.steps, args.warmup, sampler)], world, dev)[0]
     clocks = sampler.stop()
     e2e = None
     if not args.no_e2e:
@@ -870,17 +909,21 @@ def main():
         ev[3].record(stream)
         phase_events.append(ev)
 
-    def timed(fn, k, w):
+    def timed(fn, k, w, sampler=None):
         for _ in range(w):
             fn()
         barrier()
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark_begin()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(k):
             fn()
         ev1.record(stream)
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark_end()
         barrier()
         return ev0.elapsed_time(ev1) / k  # ms per step
 
@@ -891,7 +934,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     sampler.start()
-    ms_lambda = timed(lambda: step(tri.MAP_LAMBDA, record=True), args.steps, 0)
+    ms_lambda = timed(lambda: step(tri.MAP_LAMBDA, record=True), args.steps, 0, sampler)
     clocks = sampler.stop()
     ms_step = max_over_ranks([ms_lambda], world, dev)[0]
     value = job_rate(world, P, ms_step)

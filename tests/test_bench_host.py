@@ -60,3 +60,24 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "3"], capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_clock_summary_keeps_the_timed_window():
+    # samples 20 ms apart: only those within the window (one interval of
+    # slack) count; throttle reasons are those seen inside it
+    import datetime
+    import bench
+    t0 = datetime.datetime(2026, 1, 1, 12, 0, 0)
+    lines = []
+    for k in range(20):
+        ts = t0 + datetime.timedelta(milliseconds=20 * k)
+        sm = 2070 if 5 <= k <= 9 else 1200
+        cap = "Active" if k == 15 else "Not Active"
+        lines.append(f"{ts:%Y/%m/%d %H:%M:%S.%f}"[:-3] + f", 0, {sm}, 2070, 900.0, 0x0, Not Active, Not Active, "
+                     f"Not Active, {cap}\n")
+    got = bench.ClockSampler.summarize(lines, t0 + datetime.timedelta(milliseconds=110),
+                                       t0 + datetime.timedelta(milliseconds=170))
+    assert got["samples"] == 20 and got["samples_in_timed_region"] == 5
+    assert got["sm_mhz"] == 2070 and got["reasons"] == []
+    everything = bench.ClockSampler.summarize(lines)
+    assert everything["samples_in_timed_region"] == 20 and everything["reasons"] == ["sw_power_cap"]
