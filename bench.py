@@ -1011,11 +1011,21 @@ def main():
                 tri.tri_edm_host(xh, oh, x, out, ws, map=tri.MAP_LAMBDA, prec=prec, n_flagged=flagged)
 
         ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), 1)], world, dev)[0]
-        # the same device-to-host copy alone on this machine: it bounds the step, and
-        # shared hosts have given anywhere from ~95 to ~195 GB/s
-        ms_copy = timed(lambda: oh.copy_(out, non_blocking=True), 2, 1)
+        # the same device-to-host copy alone on this machine (it bounds the step):
+        # in the 16 row bands of ~512 MB that tri_edm_host copies, and as one
+        # 8.59 GB copy (shared hosts have given ~90 to ~195 GB/s for the latter)
+        nb = 16
+        edges = [0] + [min(P, int(P * (k + 1) / nb)) for k in range(nb)]
+
+        def banded():
+            for a, b in zip(edges[:-1], edges[1:]):
+                oh[a:b].copy_(out[a:b], non_blocking=True)
+        ms_copy = timed(banded, 2, 1)
+        ms_copy1 = timed(lambda: oh.copy_(out, non_blocking=True), 2, 1)
         e2e = {"value": job_rate(world, P, ms_e2e), "ms_per_step": ms_e2e,
-               "d2h_copy_alone_gbs": oh.numel() * 4 / (ms_copy * 1e-3) / 1e9, "unit": "pairs/s", "h2d_bytes_per_step": xh.numel() * 4,
+               "d2h_copy_alone_gbs": oh.numel() * 4 / (ms_copy * 1e-3) / 1e9,
+               "d2h_single_copy_gbs": oh.numel() * 4 / (ms_copy1 * 1e-3) / 1e9,
+               "unit": "pairs/s", "h2d_bytes_per_step": xh.numel() * 4,
                "d2h_bytes_per_step": oh.numel() * 4,
                "path": "tri_edm_host" if prec != tri.FP32 else "copies around tri_edm"}
         del oh, xh
