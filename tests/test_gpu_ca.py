@@ -71,7 +71,7 @@ def test_ca_rejects_unaligned_buffers():
     assert e.value.status == t.TRI_EINVAL
 
 
-def test_ca_c1_size_one_step(orc):
+def test_ca_n16384_one_step(orc):
     # the n = 16384 triangle (134,225,920 cells) of the Life workload: one step, every cell
     t = tri()
     n = 16384
@@ -92,7 +92,7 @@ def test_ca_hundred_steps(orc):
         assert np.array_equal(_run(t, g, n, 100, m, rho), ref)
 
 
-def test_ca_c1_hundred_steps_full_size(orc):
+def test_ca_n16384_hundred_steps(orc):
     # the Life workload as configured: the n = 16384 triangle, Bernoulli(0.5)
     # cells, 100 synchronous steps, every cell bit-exact after the last step,
     # under lambda and the bounding box at the tile the bench times (rho = 32)

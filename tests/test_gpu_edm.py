@@ -44,7 +44,7 @@ def test_edm_fp32_all_maps(orc, mapname, rho, reg):
         assert rel_err(got, orc.edm_packed(x)) <= TOL, (mapname, n, d, rho, reg)
 
 
-def test_edm_c0_paper_workload_full(orc):
+def test_edm_n2048_d3_every_pair(orc):
     # N = 2048 points in [0,1)^3, rho = 16: every one of the 2,098,176 pairs, lambda and BB
     t = tri()
     x = inputs.edm_uniform_points(2048, 3, seed=1609)

@@ -40,7 +40,7 @@ def test_at_energy_closed_form_tetrahedron():
     assert got == pytest.approx(4 * 1.375 / (2 * np.sqrt(2.0)) ** 9, rel=1e-6)
 
 
-def test_at_energy_c4_largest(orc):
+def test_at_energy_n1536_largest(orc):
     t = tri()
     p = inputs.at_points(1536, seed=1610)
     ref, scale = orc.at_energy(p)
