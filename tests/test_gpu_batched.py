@@ -44,6 +44,24 @@ def test_batched_matches_oracle(orc, rho, reg):
         assert rel_err(got, orc.edm_packed(xk)) <= 1e-5, k
 
 
+@pytest.mark.parametrize("rho,reg", [(16, 8), (32, 4), (8, 2)])
+def test_batched_pipelined_ragged_features(orc, rho, reg):
+    # d = 70: two full 32-feature passes and a 6-feature tail, copied in while
+    # the previous pass is computed; instances of 0 and 1 points among them
+    t = tri()
+    sizes = inputs.batched_sizes(30, lo=1, hi=500, seed=rho + reg)
+    sizes[2] = 0
+    sizes[5] = 1
+    x, pt_off, out_off, o = _batched(t, sizes, 70, rho, reg, seed=11)
+    for k, nk in enumerate(sizes):
+        nk = int(nk)
+        if nk == 0:
+            continue
+        xk = x[int(pt_off[k]): int(pt_off[k]) + nk]
+        got = o[int(out_off[k]): int(out_off[k]) + nk * (nk + 1) // 2]
+        assert rel_err(got, orc.edm_packed(xk)) <= 1e-5, (rho, reg, k)
+
+
 def test_batched_thousand_instances_every_pair(orc):
     # the 1000-instance batch (N log-uniform in [64, 8192], d = 64, seed 1609):
     # every pair of every instance against the FP64 oracle, at rho = 32 (the

@@ -34,7 +34,7 @@ def test_edm_fp32_all_maps(orc, mapname, rho, reg):
     t = tri()
     map_id = getattr(t, "MAP_" + mapname)
     S = rho * reg
-    for n, d in [(1, 3), (2, 1), (S - 1, 3), (S + 1, 4), (3 * S + 5, 33), (300, 128), (1024, 3)]:
+    for n, d in [(1, 3), (2, 1), (S - 1, 3), (S + 1, 4), (3 * S + 5, 33), (2 * S + 3, 100), (300, 128), (1024, 3)]:
         if mapname == "REC":
             m = -(-n // S)
             if m & (m - 1):
