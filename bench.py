@@ -845,6 +845,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if (args.n, args.d) != (N_PTS, D_FEAT):  # a smaller case, for profiling and tests
+        N_PTS, D_FEAT = args.n, args.d
+        WORKLOAD = f"edm_n{N_PTS}_d{D_FEAT}_normal_dup1pct"
 
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -860,9 +863,6 @@ def main():
             ap.error("--split runs the tensor-core path (bf16x3 or bf16x6)")
         run_split(args, rank, world, local)
         return
-    if (args.n, args.d) != (N_PTS, D_FEAT):
-        N_PTS, D_FEAT = args.n, args.d
-        WORKLOAD = f"edm_n{N_PTS}_d{D_FEAT}_normal_dup1pct"
 
     import torch
     import torch.distributed as dist
