@@ -299,8 +299,10 @@ TRI_API int tri_edm_rows(const float *x, uint32_t n, uint32_t d, uint32_t row_be
  *   out_cat (device FP32) / out_off (device uint64 [count]): instance k's
  *   packed triangle starts at out_cat + out_off[k].
  *   rho in {8,16,32}, reg in {1,2,4,8} as in tri_edm (FP32 direct differences).
- *   workspace: tri_edm_batched_workspace_size bytes.  Issues two kernels and
- *   no host synchronisation, so it can be captured in a CUDA graph.
+ *   workspace: tri_edm_batched_workspace_size bytes, 16-byte aligned (a
+ *   status word, a tile counter and the block offsets; the call clears the
+ *   first 16 bytes itself).  Issues a 16-byte memset and two kernels and no
+ *   host synchronisation, so it can be captured in a CUDA graph.
  *   Errors: TRI_EINVAL, TRI_ENOSPACE, TRI_ECUDA; an instance whose block count
  *   overflows 32 bits sets device status word ws[0] to TRI_ERANGE and is skipped.
  */

@@ -62,17 +62,40 @@ def test_batched_pipelined_ragged_features(orc, rho, reg):
         assert rel_err(got, orc.edm_packed(xk)) <= 1e-5, (rho, reg, k)
 
 
+ALL_TILES = [(8, 1), (8, 2), (8, 4), (8, 8), (16, 1), (16, 2), (16, 4), (16, 8), (32, 1), (32, 2), (32, 4)]
+
+
+@pytest.mark.parametrize("d", [17, 70])
+@pytest.mark.parametrize("rho,reg", ALL_TILES)
+def test_batched_every_tile_shape(orc, rho, reg, d):
+    # instance sizes q S + r (S = rho reg, q = 0, 1, 2) with r stepping through
+    # 1 .. S, so that an instance's last row block holds every count of live
+    # row groups and its diagonal blocks are both full and ragged; d = 17 is
+    # one plain pass, d = 70 the pipelined passes with a 6-feature tail
+    t = tri()
+    S = rho * reg
+    sizes = np.array([S * (k % 3) + r for k, r in enumerate(range(1, S + 1, max(1, rho // 2)))], dtype=np.int64)
+    x, pt_off, out_off, o = _batched(t, sizes, d, rho, reg, seed=rho * 100 + reg + d)
+    for k, nk in enumerate(sizes):
+        nk = int(nk)
+        xk = x[int(pt_off[k]): int(pt_off[k]) + nk]
+        got = o[int(out_off[k]): int(out_off[k]) + nk * (nk + 1) // 2]
+        assert rel_err(got, orc.edm_packed(xk)) <= 1e-5, (rho, reg, d, k, nk)
+
+
 def test_batched_thousand_instances_every_pair(orc):
     # the 1000-instance batch (N log-uniform in [64, 8192], d = 64, seed 1609):
-    # every pair of every instance against the FP64 oracle, at rho = 32 (the
-    # bench's launch) and rho = 16
+    # every pair of every instance against the FP64 oracle, at rho = 16 with
+    # 8 x 8 pairs per thread (the tuned launch the bench times) and rho = 32
+    # with 4 x 4
     t = tri()
     sizes = inputs.batched_sizes(1000, seed=1609)
-    runs = [_batched(t, sizes, 64, rho, 4, seed=1609) for rho in (32, 16)]
+    tiles = ((16, 8), (32, 4))
+    runs = [_batched(t, sizes, 64, rho, reg, seed=1609) for rho, reg in tiles]
     x, pt_off, out_off, _ = runs[0]
     for k, nk in enumerate(sizes):
         nk = int(nk)
         ref = orc.edm_packed(x[int(pt_off[k]): int(pt_off[k]) + nk])
-        for rho, (_, _, _, o) in zip((32, 16), runs):
+        for tile, (_, _, _, o) in zip(tiles, runs):
             got = o[int(out_off[k]): int(out_off[k]) + nk * (nk + 1) // 2]
-            assert rel_err(got, ref) <= 1e-5, (rho, k)
+            assert rel_err(got, ref) <= 1e-5, (tile, k)
