@@ -1011,6 +1011,16 @@ def main():
                 tri.tri_edm_host(xh, oh, x, out, ws, map=tri.MAP_LAMBDA, prec=prec, n_flagged=flagged)
 
         ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), 1)], world, dev)[0]
+        # the same steps one by one (the host link is shared with the machine's
+        # other jobs: a slow step shows here rather than only in the mean)
+        step_ms = []
+        for _ in range(3):
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            e2e_step()
+            eb.record(stream)
+            eb.synchronize()
+            step_ms.append(ea.elapsed_time(eb))
         # the same device-to-host copy alone on this machine (it bounds the step):
         # in the 16 row bands of ~512 MB that tri_edm_host copies, and as one
         # 8.59 GB copy (shared hosts have given ~90 to ~195 GB/s for the latter)
@@ -1025,6 +1035,7 @@ def main():
         e2e = {"value": job_rate(world, P, ms_e2e), "ms_per_step": ms_e2e,
                "d2h_copy_alone_gbs": oh.numel() * 4 / (ms_copy * 1e-3) / 1e9,
                "d2h_single_copy_gbs": oh.numel() * 4 / (ms_copy1 * 1e-3) / 1e9,
+               "single_steps_ms": step_ms, "copy_alone_ms": ms_copy,
                "unit": "pairs/s", "h2d_bytes_per_step": xh.numel() * 4,
                "d2h_bytes_per_step": oh.numel() * 4,
                "path": "tri_edm_host" if prec != tri.FP32 else "copies around tri_edm"}

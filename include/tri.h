@@ -313,6 +313,22 @@ TRI_API int tri_edm_batched(const float *x_cat, const uint64_t *pt_off, const ui
 TRI_API int tri_edm_batched_workspace_size(uint32_t count, size_t *bytes);
 
 /*
+ * tri_edm_batched_partition -- host only, no device work: the instances
+ * [*k_begin, *k_end) of a batch that rank `rank` of `ranks` computes, one
+ * process per GPU.  With B_k = T(ceil(n_k / (rho reg))) the block count of
+ * instance k and P_k = B_0 + ... + B_{k-1}, rank r takes the instances whose
+ * P_k lies in [r / ranks, (r + 1) / ranks) of the total: whole instances,
+ * contiguous, disjoint and in rank order, the ranges covering [0, count); a
+ * rank may get none.  The rank then calls tri_edm_batched on its slices of
+ * pt_off, n_k and out_off (count = *k_end - *k_begin); the instances' outputs
+ * are disjoint, so nothing is exchanged.
+ *   n_k (HOST uint32 [count]); rho, reg as in tri_edm_batched.
+ *   Errors: TRI_EINVAL (null pointer, ranks = 0, rank >= ranks, bad rho or reg).
+ */
+TRI_API int tri_edm_batched_partition(const uint32_t *n_k, uint32_t count, uint32_t rho, uint32_t reg,
+                                      uint32_t ranks, uint32_t rank, uint32_t *k_begin, uint32_t *k_end);
+
+/*
  * tri_ca_step -- one synchronous step of an outer-totalistic cellular
  * automaton (Game of Life: birth_mask = 1<<3, survive_mask = 1<<2 | 1<<3) on
  * the triangular domain {0 <= j <= i < n} (Section 1 lists cellular automata
@@ -333,6 +349,35 @@ TRI_API int tri_edm_batched_workspace_size(uint32_t count, size_t *bytes);
 TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
                 uint32_t birth_mask, uint32_t survive_mask, int map, uint32_t rho,
                 void *stream);
+
+/*
+ * One cellular-automaton grid split across processes, one per GPU, in row
+ * bands.  lambda numbers the tiles row by row (Section 3.1), so the tiles of
+ * block rows [R0, R1) are the numbers [T(R0), T(R1)), T(R) = R(R+1)/2.  Each
+ * step a band needs one row beyond each of its edges from the neighbouring
+ * bands (the halo), and nothing else.
+ *
+ *   tri_ca_partition: host only, no device work.  The rows [*row_begin,
+ *     *row_end) of rank `rank` of `ranks`: whole block rows of 4 rho cells,
+ *     the band of rank r starting at the first block row R with T(R) >= r /
+ *     ranks of the T(m) tiles, m = ceil(n / (4 rho)).  Bands are disjoint,
+ *     cover [0, n) in rank order and hold equal tile counts to within one
+ *     block row; a rank may get an empty band when n is small.
+ *     Errors: TRI_EINVAL (null pointer, ranks = 0, rank >= ranks, bad rho).
+ *
+ *   tri_ca_step_rows: tri_ca_step (map lambda) restricted to rows [row_begin,
+ *     row_end): only those rows' domain cells of `out` are written, and only
+ *     rows row_begin - 1 .. row_end of `in` (those inside [0, n)) are read,
+ *     so a rank's buffers need hold only its band and the two halo rows.
+ *     row_begin must be a multiple of 4 rho, row_end one too or n.  An empty
+ *     band (row_begin = row_end, n included) does nothing.  Buffers, rule, rho and errors as tri_ca_step, and
+ *     TRI_EINVAL for a band that is not whole block rows or not inside [0, n].
+ */
+TRI_API int tri_ca_partition(uint32_t n, uint32_t rho, uint32_t ranks, uint32_t rank,
+                             uint32_t *row_begin, uint32_t *row_end);
+TRI_API int tri_ca_step_rows(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
+                             uint32_t birth_mask, uint32_t survive_mask, uint32_t rho,
+                             uint32_t row_begin, uint32_t row_end, void *stream);
 
 /*
  * tri_collide -- collision detection of N spheres (Section 5, test 3): every
@@ -409,6 +454,36 @@ TRI_API int tet_map_ex(int map, uint32_t n, uint32_t rho, int body, uint32_t *ou
 TRI_API int tet_at_energy(const float *xyz, uint32_t n, double nu, double *energy, int map,
                   uint32_t rho, void *workspace, size_t ws_bytes, void *stream);
 TRI_API int tet_at_workspace_size(uint32_t n, uint32_t rho, int map, size_t *bytes);
+
+/*
+ * One Axilrod-Teller energy split across processes, one per GPU: each rank
+ * sums the triplets of a contiguous range of the tetrahedral block numbers
+ * (Section 6: block w = T3(L) + T(R) + C, T3(L) = L(L+1)(L+2)/6, with m =
+ * ceil(n / rho) layers), and the ranks add their partial energies (one FP64
+ * all-reduce).
+ *
+ *   tet_at_partition: host only, no device work.  The blocks
+ *     [*omega_begin, *omega_end) = [floor(T k / ranks), floor(T (k+1) /
+ *     ranks)) of the T = T3(m) blocks for k = rank: disjoint, covering [0, T)
+ *     in rank order.  Errors: TRI_EINVAL (null pointer, ranks = 0, rank >=
+ *     ranks, bad rho), TRI_ERANGE (T >= 2^32).
+ *
+ *   tet_at_energy_range: the energy of the strict triplets in blocks
+ *     [omega_begin, omega_end), written to *energy (device, one double): block
+ *     partials in FP64, then a fixed-order sum, as tet_at_energy.  An empty
+ *     range gives 0.  The ranges of any partition of [0, T) add up to
+ *     tet_at_energy's result up to the order of the FP64 additions.
+ *     map: TRI_MAP_LAMBDA or TRI_MAP_TET_TABLE.  workspace: device, 8-byte
+ *     aligned, at least (omega_end - omega_begin) doubles.
+ *     Errors: TRI_EINVAL (null pointer, n = 0, bad rho or map, omega_begin >
+ *     omega_end or omega_end > T), TRI_ENOSPACE, TRI_ERANGE (T >= 2^32),
+ *     TRI_ECUDA.
+ */
+TRI_API int tet_at_partition(uint32_t n, uint32_t rho, uint32_t ranks, uint32_t rank,
+                             uint64_t *omega_begin, uint64_t *omega_end);
+TRI_API int tet_at_energy_range(const float *xyz, uint32_t n, double nu, double *energy, int map,
+                                uint32_t rho, uint64_t omega_begin, uint64_t omega_end,
+                                void *workspace, size_t ws_bytes, void *stream);
 
 /*
  * tet_at_energy_noalloc -- tet_at_energy without a workspace, for callers

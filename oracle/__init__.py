@@ -21,6 +21,9 @@ Parity status per function (which pin ties it to something outside itself):
   at_energy                 pinned: equilateral, collinear and right-isosceles
                             closed forms; invariance under rigid motion and
                             permutation.
+  at_energy_blocks          pinned: each block's energy equals the sum of the
+                            three-point energies of its triplets, found through
+                            tet_enum's order; the whole range gives at_energy.
   collide_*                 pinned: exact integer brute force on inputs where
                             FP32 is exact, a touching lattice (closed-form
                             neighbour counts), an interval sweep in 1-D,
@@ -61,6 +64,8 @@ def lib():
         L.orc_ca_run.argtypes = [vp, vp, i64, i64, ctypes.c_uint32, ctypes.c_uint32, i64]
         L.orc_at_energy.argtypes = [vp, i64, ctypes.c_double, vp]
         L.orc_at_energy.restype = ctypes.c_double
+        L.orc_at_energy_blocks.argtypes = [vp, i64, ctypes.c_double, i64, i64, i64, vp]
+        L.orc_at_energy_blocks.restype = ctypes.c_double
         L.orc_collide_rows.argtypes = [vp, vp, i64, i64, i64, vp]
         L.orc_collide_pairs.argtypes = [vp, vp, i64, i64, i64, vp, vp, vp]
         L.orc_collide_count_of.argtypes = [vp, vp, i64, i64, vp, i64, vp]
@@ -175,6 +180,15 @@ def at_energy(p: np.ndarray, nu: float = 1.0):
     p = np.ascontiguousarray(p, dtype=np.float32)
     a = np.zeros(1, dtype=np.float64)
     e = lib().orc_at_energy(_p(p), p.shape[0], float(nu), _p(a))
+    return float(e), float(a[0])
+
+
+def at_energy_blocks(p: np.ndarray, rho: int, w0: int, w1: int, nu: float = 1.0):
+    """(E, sum |term|) over the triplets whose tetrahedral block (i / rho, j /
+    rho, k / rho) has a number in [w0, w1) of the order of tet_enum (Section 6)."""
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    a = np.zeros(1, dtype=np.float64)
+    e = lib().orc_at_energy_blocks(_p(p), p.shape[0], float(nu), int(rho), int(w0), int(w1), _p(a))
     return float(e), float(a[0])
 
 

@@ -227,6 +227,53 @@ double orc_at_energy(const float *p, int64_t n, double nu, double *abs_sum)
     return e;
 }
 
+/* The same energy over the triplets of a range of tetrahedral blocks only:
+ * the triplet i > j > k lies in block (L, R, C) = (i / rho, j / rho, k / rho),
+ * L >= R >= C, whose number in the order of orc_tet_enum (layer L, then row
+ * R <= L, then column C <= R; Section 6) is the count of blocks before it,
+ *     w = L(L+1)(L+2)/6 + R(R+1)/2 + C,
+ * and the triplet counts when w0 <= w < w1.  The terms of one i are added in
+ * the order of orc_at_energy, so the whole range [0, T_m) gives its result
+ * bit for bit. */
+double orc_at_energy_blocks(const float *p, int64_t n, double nu, int64_t rho, int64_t w0, int64_t w1,
+                            double *abs_sum)
+{
+    double *part = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *apart = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0, sa = 0.0;
+        const int64_t L = i / rho;
+        for (int64_t j = 0; j < i; ++j) {
+            const int64_t R = j / rho;
+            for (int64_t k = 0; k < j; ++k) {
+                const int64_t C = k / rho;
+                const int64_t w = L * (L + 1) * (L + 2) / 6 + R * (R + 1) / 2 + C;
+                if (w < w0 || w >= w1)
+                    continue;
+                double t = orc_at_term(p, i, j, k, nu);
+                s += t;
+                sa += fabs(t);
+            }
+        }
+        part[i] = s;
+        apart[i] = sa;
+    }
+    double e = 0.0, comp = 0.0, ea = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double y = part[i] - comp;
+        double t = e + y;
+        comp = (t - e) - y;
+        e = t;
+        ea += apart[i];
+    }
+    free(part);
+    free(apart);
+    if (abs_sum)
+        *abs_sum = ea;
+    return e;
+}
+
 /* ------------------------------------------------------------------------
  * Section 5, test 3: collision detection of N spheres with random radii.
  * Spheres i and j (i > j) collide when the distance between their centres is

@@ -24,12 +24,13 @@ namespace {
 constexpr int AT_ROWS = 2;
 
 template <int MAP>
-__global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, uint32_t m, uint64_t nblocks,
-                          double *__restrict__ partial)
+__global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, uint32_t m, uint64_t w0,
+                          uint64_t nblocks, double *__restrict__ partial)
 {
     uint32_t L, R, C;
     if constexpr (MAP == MAP_LAMBDA || MAP == MAP_TET_TABLE) {
-        const uint64_t w = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        // blocks [w0, nblocks) of the tetrahedral numbering, one per grid position
+        const uint64_t w = w0 + (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
         if (w >= nblocks) return;
         if constexpr (MAP == MAP_TET_TABLE) tet_block_table((uint32_t)w, m, L, R, C);
         else tet_block((uint32_t)w, L, R, C);
@@ -138,7 +139,7 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
     if (tid == 0) {
         double t = 0.0;
         for (uint32_t q = 0; q < (nthreads + 31) / 32; ++q) t += wsum[q];
-        partial[T3(L) + T2(R) + C] = nu * t;
+        partial[T3(L) + T2(R) + C - w0] = nu * t;
     }
 }
 
@@ -172,24 +173,28 @@ extern "C" int tet_at_workspace_size(uint32_t n, uint32_t rho, int map, size_t *
     return TRI_OK;
 }
 
-// Launches the partial-sum kernel into `partial` (at least T3(m) doubles) and
-// the fixed-order reduction into *energy.
+// Launches the partial-sum kernel over blocks [w0, w1) of the tetrahedral
+// numbering (all T3(m) blocks for the box) into `partial` (at least w1 - w0
+// doubles, block w at w - w0) and the fixed-order reduction into *energy.
 static int at_energy_launch(const float *xyz, uint32_t n, double nu, double *energy, int map, uint32_t rho,
-                      double *partial, cudaStream_t s)
+                            uint64_t w0, uint64_t w1, double *partial, cudaStream_t s)
 {
     const uint64_t m = ((uint64_t)n + rho - 1) / rho;
-    const uint64_t nb = T3(m);
+    const uint64_t nb = w1 - w0;
     const dim3 blk(rho, rho / AT_ROWS);
     if (map == TRI_MAP_LAMBDA || map == TRI_MAP_TET_TABLE) {
-        if (nb > 0xFFFFFFFFull) return TRI_ERANGE;
-        if (map == TRI_MAP_LAMBDA)
-            at_kernel<MAP_LAMBDA><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, nb, partial);
-        else
-            at_kernel<MAP_TET_TABLE><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, nb,
-                                                                               partial);
+        if (w1 > 0xFFFFFFFFull) return TRI_ERANGE;
+        if (nb > 0) {
+            if (map == TRI_MAP_LAMBDA)
+                at_kernel<MAP_LAMBDA><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, w0, w1,
+                                                                                partial);
+            else
+                at_kernel<MAP_TET_TABLE><<<trihost::linear_grid(nb), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, w0, w1,
+                                                                                   partial);
+        }
     } else {
         if (m > 65535) return TRI_ERANGE;
-        at_kernel<MAP_BB><<<dim3((unsigned)m, (unsigned)m, (unsigned)m), blk, 0, s>>>(xyz, n, nu, (uint32_t)m,
+        at_kernel<MAP_BB><<<dim3((unsigned)m, (unsigned)m, (unsigned)m), blk, 0, s>>>(xyz, n, nu, (uint32_t)m, 0,
                                                                                         nb, partial);
     }
     if (cudaGetLastError() != cudaSuccess) return TRI_ECUDA;
@@ -205,7 +210,38 @@ extern "C" int tet_at_energy(const float *xyz, uint32_t n, double nu, double *en
     size_t need = 0;
     tet_at_workspace_size(n, rho, map, &need);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 7)) return TRI_ENOSPACE;
-    return at_energy_launch(xyz, n, nu, energy, map, rho, (double *)workspace, (cudaStream_t)stream);
+    const uint64_t m = ((uint64_t)n + rho - 1) / rho;
+    return at_energy_launch(xyz, n, nu, energy, map, rho, 0, T3(m), (double *)workspace, (cudaStream_t)stream);
+}
+
+// The tetrahedral block range of one of several GPUs: [floor(T k / ranks),
+// floor(T (k + 1) / ranks)) of the T = T3(m) blocks, in lambda's numbering.
+extern "C" int tet_at_partition(uint32_t n, uint32_t rho, uint32_t ranks, uint32_t rank, uint64_t *omega_begin,
+                                uint64_t *omega_end)
+{
+    if (!omega_begin || !omega_end || ranks == 0 || rank >= ranks || !trihost::rho_ok(rho)) return TRI_EINVAL;
+    const uint64_t m = ((uint64_t)n + rho - 1) / rho, T = T3(m);
+    if (T > 0xFFFFFFFFull) return TRI_ERANGE;
+    // floor(T k / ranks) without overflow: T = q ranks + r
+    const uint64_t q = T / ranks, r = T % ranks;
+    auto edge = [&](uint64_t k) { return q * k + r * k / ranks; };
+    *omega_begin = edge(rank);
+    *omega_end = edge(rank + 1);
+    return TRI_OK;
+}
+
+extern "C" int tet_at_energy_range(const float *xyz, uint32_t n, double nu, double *energy, int map, uint32_t rho,
+                                   uint64_t omega_begin, uint64_t omega_end, void *workspace, size_t ws_bytes,
+                                   void *stream)
+{
+    if (!xyz || !energy || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
+    if (map != TRI_MAP_LAMBDA && map != TRI_MAP_TET_TABLE) return TRI_EINVAL;
+    const uint64_t m = ((uint64_t)n + rho - 1) / rho;
+    if (omega_begin > omega_end || omega_end > T3(m)) return TRI_EINVAL;
+    if (!workspace || ws_bytes < (omega_end - omega_begin) * sizeof(double) || ((uintptr_t)workspace & 7))
+        return TRI_ENOSPACE;
+    return at_energy_launch(xyz, n, nu, energy, map, rho, omega_begin, omega_end, (double *)workspace,
+                            (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,5 +297,6 @@ extern "C" int tet_at_energy_noalloc(const float *xyz, uint32_t n, double nu, do
     if (st != TRI_OK) return st;
     // Every partial the reduction reads is written by this call's first
     // kernel, so nothing in the array needs clearing between calls.
-    return at_energy_launch(xyz, n, nu, energy, map, rho, partial, (cudaStream_t)stream);
+    const uint64_t m = ((uint64_t)n + rho - 1) / rho;
+    return at_energy_launch(xyz, n, nu, energy, map, rho, 0, T3(m), partial, (cudaStream_t)stream);
 }

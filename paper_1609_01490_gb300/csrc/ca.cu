@@ -4,6 +4,7 @@
 // automaton that Section 1 lists among the TD problems).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "tri_maps.cuh"
@@ -294,8 +295,9 @@ cudaError_t launch_rho(uint32_t rho, dim3 g, cudaStream_t s, const uint8_t *in, 
 
 }  // namespace
 
-extern "C" int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld, uint32_t birth_mask,
-                           uint32_t survive_mask, int map, uint32_t rho, void *stream)
+// The checks every step call makes: buffers, alignment, no aliasing, masks.
+static int ca_args_ok(const uint8_t *in, const uint8_t *out, uint32_t n, size_t ld, uint32_t birth_mask,
+                      uint32_t survive_mask, uint32_t rho)
 {
     if (!in || !out || n == 0 || !trihost::rho_ok(rho)) return TRI_EINVAL;
     if (ld < n || (ld & 15) || ((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return TRI_EINVAL;
@@ -303,6 +305,14 @@ extern "C" int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t l
     const size_t span = (size_t)(n - 1) * ld + n;
     if ((in < out + span) && (out < in + span)) return TRI_EINVAL;
     if ((birth_mask | survive_mask) >> 9) return TRI_EINVAL;
+    return TRI_OK;
+}
+
+extern "C" int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld, uint32_t birth_mask,
+                           uint32_t survive_mask, int map, uint32_t rho, void *stream)
+{
+    const int ok = ca_args_ok(in, out, n, ld, birth_mask, survive_mask, rho);
+    if (ok != TRI_OK) return ok;
     const uint32_t table = birth_mask | (survive_mask << 9);  // bit count + 9*alive
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t S = 4 * rho, m = (n + S - 1) / S;
@@ -340,5 +350,54 @@ extern "C" int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t l
     default:
         return TRI_EINVAL;
     }
+    return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
+}
+
+// Row bands of one grid for several GPUs: band k holds the block rows from
+// the first whose lambda number T(R) reaches k / ranks of the T(m) tiles, so
+// the bands hold equal tile counts to within one block row.
+extern "C" int tri_ca_partition(uint32_t n, uint32_t rho, uint32_t ranks, uint32_t rank, uint32_t *row_begin,
+                                uint32_t *row_end)
+{
+    if (!row_begin || !row_end || ranks == 0 || rank >= ranks || !trihost::rho_ok(rho)) return TRI_EINVAL;
+    const uint32_t S = 4 * rho, m = (uint32_t)(((uint64_t)n + S - 1) / S);
+    const uint64_t total = T2(m);
+    auto edge = [&](uint32_t k) -> uint32_t {
+        if (k >= ranks) return m;
+        const long double target = (long double)total * k / ranks;
+        uint32_t lo = 0, hi = m;  // smallest R in [0, m] with T(R) >= target
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) / 2;
+            if ((long double)T2(mid) >= target) hi = mid;
+            else lo = mid + 1;
+        }
+        return lo;
+    };
+    *row_begin = (uint32_t)std::min<uint64_t>(n, (uint64_t)S * edge(rank));
+    *row_end = (uint32_t)std::min<uint64_t>(n, (uint64_t)S * edge(rank + 1));
+    return TRI_OK;
+}
+
+// One step of rows [row_begin, row_end) only: the lambda blocks of those
+// block rows, numbers [T(R0), T(R1)), read rows row_begin - 1 .. row_end of
+// `in` (those inside the grid) and write the band's domain cells of `out`.
+extern "C" int tri_ca_step_rows(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld, uint32_t birth_mask,
+                                uint32_t survive_mask, uint32_t rho, uint32_t row_begin, uint32_t row_end,
+                                void *stream)
+{
+    const int ok = ca_args_ok(in, out, n, ld, birth_mask, survive_mask, rho);
+    if (ok != TRI_OK) return ok;
+    const uint32_t S = 4 * rho;
+    if (row_begin > row_end || row_end > n) return TRI_EINVAL;
+    if (row_begin == row_end) return TRI_OK;  // an empty band (also one at row n) does nothing
+    if (row_begin % S != 0 || (row_end % S != 0 && row_end != n)) return TRI_EINVAL;
+    const uint32_t table = birth_mask | (survive_mask << 9);
+    const uint32_t m = (n + S - 1) / S, R0 = row_begin / S, R1 = (row_end + S - 1) / S;
+    BlockMap bm{};
+    bm.m = m;
+    bm.w0 = T2(R0);
+    bm.nblocks = T2(R1);
+    const cudaError_t e = launch_rho<MAP_LAMBDA>(rho, trihost::linear_grid(bm.nblocks - bm.w0),
+                                                 (cudaStream_t)stream, in, out, n, ld, table, bm);
     return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }

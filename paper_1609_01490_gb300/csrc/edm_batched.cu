@@ -203,3 +203,34 @@ extern "C" int tri_edm_batched(const float *x_cat, const uint64_t *pt_off, const
 #undef TRI_B
     return e == cudaSuccess ? TRI_OK : TRI_ECUDA;
 }
+
+// Instances of one batch for several GPUs: with B_k = T(ceil(n_k / S)) the
+// block count of instance k (S = rho reg) and P_k = B_0 + ... + B_{k-1}, rank
+// r takes the instances k whose P_k lies in [r / ranks, (r + 1) / ranks) of
+// the total, each whole: its own slices of pt_off, n_k and out_off, no shared
+// output.
+extern "C" int tri_edm_batched_partition(const uint32_t *n_k, uint32_t count, uint32_t rho, uint32_t reg,
+                                         uint32_t ranks, uint32_t rank, uint32_t *k_begin, uint32_t *k_end)
+{
+    if ((!n_k && count > 0) || !k_begin || !k_end || ranks == 0 || rank >= ranks) return TRI_EINVAL;
+    if (!trihost::rho_ok(rho) || (reg != 1 && reg != 2 && reg != 4 && reg != 8) || (reg == 8 && rho > 16))
+        return TRI_EINVAL;
+    const uint64_t S = (uint64_t)rho * reg;
+    uint64_t total = 0;
+    for (uint32_t k = 0; k < count; ++k) total += T2((n_k[k] + S - 1) / S);
+    // first instance whose prefix reaches share r of the total (count if none)
+    auto edge = [&](uint32_t r) -> uint32_t {
+        if (r == 0) return 0;
+        if (r >= ranks) return count;
+        const long double target = (long double)total * r / ranks;
+        uint64_t run = 0;
+        for (uint32_t k = 0; k < count; ++k) {
+            if ((long double)run >= target) return k;
+            run += T2((n_k[k] + S - 1) / S);
+        }
+        return count;
+    };
+    *k_begin = edge(rank);
+    *k_end = edge(rank + 1);
+    return TRI_OK;
+}

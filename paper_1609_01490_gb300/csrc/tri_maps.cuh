@@ -93,9 +93,11 @@ __device__ __forceinline__ void lambda_nodiag(uint32_t w, uint32_t &i, uint32_t 
 // A block map turns blockIdx into a block (bi, bj) of the with-diagonal
 // triangle of m block rows, or reports that the block has no work.
 struct BlockMap {
-    uint64_t nblocks;  // lambda: m(m+1)/2
+    uint64_t nblocks;  // lambda: one past the last block number (m(m+1)/2 for the whole triangle)
     uint32_t m;        // block rows of the triangle
     uint32_t level;    // REC: 0 = diagonal pass, l >= 1 = squares of side 2^(l-1)
+    uint64_t w0;       // lambda: the block number of grid position 0 (a band of block rows
+                       // [R0, R1) is the range [T(R0), T(R1)) of lambda's numbering)
 };
 
 enum : int {
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool map_block_at(const BlockMap &a, uint32_t bx, uin
 {
     if constexpr (MAP == MAP_LAMBDA || MAP == MAP_LAMBDA_PD || MAP == MAP_LAMBDA_ND) {
         // omega from the (1-D, 2-D or P_Delta) grid, row-major over the grid
-        const uint64_t w = (uint64_t)by * gx + bx;
+        const uint64_t w = a.w0 + (uint64_t)by * gx + bx;
         if (w >= a.nblocks) return false;
         if constexpr (MAP == MAP_LAMBDA_ND) {
             uint32_t I;

@@ -64,13 +64,18 @@ _SIGS = {
     "tri_edm_rows": ([_vp, _u32, _u32, _u32, _u32, _vp, _i32, _i32, _vp, _sz, _vp, _vp], _i32),
     "tri_edm_batched": ([_vp, _vp, _vp, _u32, _u32, _vp, _vp, _u32, _u32, _vp, _sz, _vp], _i32),
     "tri_edm_batched_workspace_size": ([_u32, _szp], _i32),
+    "tri_edm_batched_partition": ([_vp, _u32, _u32, _u32, _u32, _u32, _vp, _vp], _i32),
     "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
+    "tri_ca_partition": ([_u32, _u32, _u32, _u32, _vp, _vp], _i32),
+    "tri_ca_step_rows": ([_vp, _vp, _u32, _sz, _u32, _u32, _u32, _u32, _u32, _vp], _i32),
     "tri_collide": ([_vp, _vp, _u32, _u32, _i32, _u32, _u32, _vp, _vp, _u64, _vp, _vp], _i32),
     "tet_map": ([_u32, _u32, _i32, _vp, _vp], _i32),
     "tet_map_ex": ([_i32, _u32, _u32, _i32, _vp, _vp], _i32),
     "tet_at_energy": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp, _sz, _vp], _i32),
     "tet_at_workspace_size": ([_u32, _u32, _i32, _szp], _i32),
     "tet_at_energy_noalloc": ([_vp, _u32, _f64, _vp, _i32, _u32, _vp], _i32),
+    "tet_at_partition": ([_u32, _u32, _u32, _u32, _vp, _vp], _i32),
+    "tet_at_energy_range": ([_vp, _u32, _f64, _vp, _i32, _u32, _u64, _u64, _vp, _sz, _vp], _i32),
     "tri_mlp_workspace_size": ([_u32, _u32, _u32, _szp], _i32),
     "tri_mlp_forward": ([_vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _sz, _vp], _i32),
     "tri_mlp_grad": ([_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp, _sz, _vp], _i32),
@@ -241,6 +246,18 @@ def tri_edm_batched(x_cat, pt_off, n_k, out_cat, out_off, rho: int = 16, reg: in
                                                    ws_bytes, _stream(stream)))
 
 
+def tri_edm_batched_partition(n_k_host, rho: int, reg: int, ranks: int, rank: int):
+    """(k_begin, k_end): the instances rank `rank` of `ranks` computes (host only;
+    n_k_host: the instance sizes as a sequence or a host array)."""
+    import numpy as np
+    nk = np.ascontiguousarray(np.asarray(n_k_host, dtype=np.uint32))
+    kb, ke = ctypes.c_uint32(), ctypes.c_uint32()
+    _check("tri_edm_batched_partition",
+           _lib.tri_edm_batched_partition(nk.ctypes.data if nk.size else None, nk.size, rho, reg, ranks, rank,
+                                          ctypes.byref(kb), ctypes.byref(ke)))
+    return kb.value, ke.value
+
+
 # -------------------------------------------------------------------- CA --
 def tri_collide(centres, radii, n_pairs, count=None, pairs=None, map: int = MAP_LAMBDA, rho: int = 16,
                 reg: int = 0, stream=None) -> None:
@@ -264,6 +281,22 @@ def tri_ca_step(inp, out, n: int, birth_mask: int = LIFE_BIRTH, survive_mask: in
                                            _stream(stream)))
 
 
+def tri_ca_partition(n: int, rho: int, ranks: int, rank: int):
+    """(row_begin, row_end) of rank `rank` of `ranks` (host only)."""
+    rb, re_ = ctypes.c_uint32(), ctypes.c_uint32()
+    _check("tri_ca_partition", _lib.tri_ca_partition(n, rho, ranks, rank, ctypes.byref(rb), ctypes.byref(re_)))
+    return rb.value, re_.value
+
+
+def tri_ca_step_rows(inp, out, n: int, row_begin: int, row_end: int, birth_mask: int = LIFE_BIRTH,
+                     survive_mask: int = LIFE_SURVIVE, rho: int = 32, stream=None) -> None:
+    ld = inp.stride(0)
+    if out.stride(0) != ld:
+        raise ValueError("in and out must share the leading dimension")
+    _check("tri_ca_step_rows", _lib.tri_ca_step_rows(_ptr(inp), _ptr(out), n, ld, birth_mask, survive_mask, rho,
+                                                     row_begin, row_end, _stream(stream)))
+
+
 # -------------------------------------------------------------------- AT --
 def tet_at_workspace_size(n: int, rho: int, map: int = MAP_LAMBDA) -> int:
     return _size(_lib.tet_at_workspace_size, n, rho, map)
@@ -282,6 +315,21 @@ def tet_at_energy_noalloc(xyz, energy, nu: float = 1.0, map: int = MAP_LAMBDA, r
     callers that cannot allocate device memory (see include/tri.h)."""
     _check("tet_at_energy_noalloc", _lib.tet_at_energy_noalloc(_ptr(xyz), xyz.shape[0], float(nu), _ptr(energy),
                                                                map, rho, _stream(stream)))
+
+
+def tet_at_partition(n: int, rho: int, ranks: int, rank: int):
+    """(omega_begin, omega_end) of rank `rank` of `ranks` (host only)."""
+    w0, w1 = ctypes.c_uint64(), ctypes.c_uint64()
+    _check("tet_at_partition", _lib.tet_at_partition(n, rho, ranks, rank, ctypes.byref(w0), ctypes.byref(w1)))
+    return w0.value, w1.value
+
+
+def tet_at_energy_range(xyz, energy, omega_begin: int, omega_end: int, nu: float = 1.0, map: int = MAP_LAMBDA,
+                        rho: int = 32, workspace=None, stream=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("tet_at_energy_range", _lib.tet_at_energy_range(_ptr(xyz), xyz.shape[0], float(nu), _ptr(energy), map,
+                                                           rho, omega_begin, omega_end, _ptr(workspace), ws_bytes,
+                                                           _stream(stream)))
 
 
 # ------------------------------------------------------------------- MLP --
