@@ -559,6 +559,27 @@ def run_suite(args):
               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                            "algorithmic_bytes_per_step": 2 * cells},
               "cpu_baseline": cpu_leg(lambda: oracle.ca_step(gh), cells, "cells/s", "one step of the n = 16384 grid")})
+        # the same 100 steps through tri_ca_run: up to 8 steps per pass through
+        # memory (tiles read once with an 8-cell halo, stepped as bits in
+        # shared memory, written once), 13 passes
+        c = torch.zeros_like(a)
+
+        def run100(m):
+            def go():
+                tri.tri_ca_run(a, b, n, 100, scratch=c, map=m, rho=32)
+            return go
+        tr = {nm: graph_ms(run100(m), 1) for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB),
+                                                        ("rb", tri.MAP_RB), ("rec", tri.MAP_REC))}
+        passes = -(-100 // 8)
+        gbs_run = 2.0 * cells * passes / (tr["lambda"] * 1e-3) / 1e9
+        emit({"row": "life_run", "metric": "cell updates/s", "unit": "cells/s",
+              "value": 100 * cells / (tr["lambda"] * 1e-3),
+              "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 32, "steps_per_pass": 8},
+              "ms_per_100_steps": tr, "I_bb_over_lambda": tr["bb"] / tr["lambda"],
+              "speedup_over_step_by_step": 100 * t["lambda"] / tr["lambda"],
+              "roofline": {"bound": "hbm", "achieved": gbs_run, "peak": hbm, "unit": "GB/s", "frac": gbs_run / hbm,
+                           "algorithmic_bytes_per_pass": 2 * cells, "passes": passes,
+                           "note": "one read and one write of every cell per pass; the 8-cell halos are re-read"}})
 
     if want("at"):
         # a7: Axilrod-Teller energy over the tetrahedral domain, N = 1536, rho = 16

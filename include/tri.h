@@ -351,6 +351,31 @@ TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
                 void *stream);
 
 /*
+ * tri_ca_run -- `steps` synchronous steps of the automaton of tri_ca_step,
+ * the result in `out`.  Conway's rule at rho = 32 (128 x 128-cell tiles) runs
+ * several steps per pass through memory: each block reads its tile with an
+ * 8-cell halo once, as bits in shared memory, takes up to 8 steps there
+ * (clearing the cells outside the domain after each) and writes the tile's
+ * domain cells once, so a pass costs about what one step of tri_ca_step
+ * costs.  Other rules and rho take one tri_ca_step per step.  The result is
+ * the same bit for bit as `steps` calls of tri_ca_step.
+ *   in (read only), out and scratch (device uint8, 16-byte aligned, row-major
+ *   with leading dimension ld as in tri_ca_step): pairwise disjoint.  scratch
+ *   holds intermediate states when more than one pass is needed (steps > 8
+ *   for the fused form, steps > 1 otherwise) and may be NULL otherwise.  Only
+ *   domain cells of out and scratch are written.
+ *   map: LAMBDA, LAMBDA_PDELTA, BB, RB or REC; rho in {8,16,32}; steps >= 1.
+ *   Issues one launch per pass (REC: one per level and pass) and no host
+ *   synchronisation.
+ *   Errors: TRI_EINVAL (null, aliasing, bad ld/rho/map/masks, steps = 0,
+ *   missing scratch), TRI_ERANGE (REC with a block count that is not a power
+ *   of two), TRI_ECUDA.
+ */
+TRI_API int tri_ca_run(const uint8_t *in, uint8_t *out, uint8_t *scratch, uint32_t n, size_t ld,
+                       uint32_t birth_mask, uint32_t survive_mask, int map, uint32_t rho,
+                       uint32_t steps, void *stream);
+
+/*
  * One cellular-automaton grid split across processes, one per GPU, in row
  * bands.  lambda numbers the tiles row by row (Section 3.1), so the tiles of
  * block rows [R0, R1) are the numbers [T(R0), T(R1)), T(R) = R(R+1)/2.  Each

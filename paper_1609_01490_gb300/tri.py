@@ -66,6 +66,7 @@ _SIGS = {
     "tri_edm_batched_workspace_size": ([_u32, _szp], _i32),
     "tri_edm_batched_partition": ([_vp, _u32, _u32, _u32, _u32, _u32, _vp, _vp], _i32),
     "tri_ca_step": ([_vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _vp], _i32),
+    "tri_ca_run": ([_vp, _vp, _vp, _u32, _sz, _u32, _u32, _i32, _u32, _u32, _vp], _i32),
     "tri_ca_partition": ([_u32, _u32, _u32, _u32, _vp, _vp], _i32),
     "tri_ca_step_rows": ([_vp, _vp, _u32, _sz, _u32, _u32, _u32, _u32, _u32, _vp], _i32),
     "tri_collide": ([_vp, _vp, _u32, _u32, _i32, _u32, _u32, _vp, _vp, _u64, _vp, _vp], _i32),
@@ -279,6 +280,15 @@ def tri_ca_step(inp, out, n: int, birth_mask: int = LIFE_BIRTH, survive_mask: in
         raise ValueError("in and out must share the leading dimension")
     _check("tri_ca_step", _lib.tri_ca_step(_ptr(inp), _ptr(out), n, ld, birth_mask, survive_mask, map, rho,
                                            _stream(stream)))
+
+
+def tri_ca_run(inp, out, n: int, steps: int, scratch=None, birth_mask: int = LIFE_BIRTH,
+               survive_mask: int = LIFE_SURVIVE, map: int = MAP_LAMBDA, rho: int = 32, stream=None) -> None:
+    ld = inp.stride(0)
+    if out.stride(0) != ld or (scratch is not None and scratch.stride(0) != ld):
+        raise ValueError("in, out and scratch must share the leading dimension")
+    _check("tri_ca_run", _lib.tri_ca_run(_ptr(inp), _ptr(out), _ptr(scratch), n, ld, birth_mask, survive_mask, map,
+                                         rho, steps, _stream(stream)))
 
 
 def tri_ca_partition(n: int, rho: int, ranks: int, rank: int):

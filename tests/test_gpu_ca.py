@@ -103,3 +103,72 @@ def test_ca_n16384_hundred_steps(orc):
     for m in (t.MAP_LAMBDA, t.MAP_BB):
         got = _run(t, g, n, 100, m, 32)
         assert np.array_equal(got, ref), m
+        # the same 100 steps in passes of up to 8 steps (tri_ca_run)
+        assert np.array_equal(_run_fused(t, g, n, 100, m, 32), ref), ("run", m)
+
+
+def _run_fused(t, g, n, steps, map_id, rho, birth=None, survive=None):
+    import torch
+    D = dev()
+    a = torch.from_numpy(g).to(D)
+    out = a.clone()        # the bytes outside the domain must come back unchanged
+    scratch = torch.full_like(a, 7)
+    kw = {}
+    if birth is not None:
+        kw = dict(birth_mask=birth, survive_mask=survive)
+    t.tri_ca_run(a, out, n, steps, scratch=scratch, map=map_id, rho=rho, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(a.cpu(), torch.from_numpy(g))  # the input is only read
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("mapname", ["LAMBDA", "LAMBDA_PDELTA", "BB", "RB", "REC"])
+def test_ca_run_fused_matches_the_oracle(orc, mapname):
+    # Conway's rule at rho = 32 runs up to 8 steps per pass: step counts below,
+    # at and across a pass, sizes around the 128-cell tile, a padded leading
+    # dimension and junk above the diagonal (outside the domain)
+    t = tri()
+    map_id = getattr(t, "MAP_" + mapname)
+    for n in (1, 5, 127, 128, 129, 300, 1000, 1024):
+        m = -(-n // 128)
+        if mapname == "REC" and m & (m - 1):
+            continue
+        ld = -(-n // 16) * 16 + (16 if n % 3 == 0 else 0)
+        g = inputs.ca_grid(n, seed=n + 3, ld=ld)
+        g[np.triu_indices(n, 1)] = 5
+        g[:, n:] = 9
+        for steps in (1, 3, 8, 9, 17):
+            got = _run_fused(t, g, n, steps, map_id, 32)
+            assert np.array_equal(got, orc.ca_run(g, steps)), (mapname, n, steps)
+
+
+def test_ca_run_other_rules_and_tiles(orc):
+    # rules other than Conway's and tiles other than rho = 32 step one launch at a time
+    t = tri()
+    n = 300
+    g = inputs.ca_grid(n, seed=11, ld=304)
+    highlife = ((1 << 3) | (1 << 6), (1 << 2) | (1 << 3))
+    for rho, rule in ((16, None), (8, None), (32, highlife), (16, highlife)):
+        b, s_ = rule if rule else (None, None)
+        got = _run_fused(t, g, n, 11, t.MAP_LAMBDA, rho, b, s_)
+        ref = orc.ca_run(g, 11, *rule) if rule else orc.ca_run(g, 11)
+        assert np.array_equal(got, ref), (rho, rule)
+
+
+def test_ca_run_errors():
+    import torch
+    t = tri()
+    n = 200
+    a = torch.zeros((n, 208), dtype=torch.uint8, device=dev())
+    b, c = torch.zeros_like(a), torch.zeros_like(a)
+    cases = [dict(steps=0, scratch=c), dict(steps=9, scratch=None), dict(steps=9, scratch=a),
+             dict(steps=3, scratch=c, map=t.MAP_UTM)]
+    for kw in cases:
+        with pytest.raises(t.TriError) as e:
+            t.tri_ca_run(a, b, n, **kw)
+        assert e.value.status == t.TRI_EINVAL, kw
+    with pytest.raises(t.TriError) as e:
+        t.tri_ca_run(a, a, n, 3)  # out is in
+    assert e.value.status == t.TRI_EINVAL
+    t.tri_ca_run(a, b, n, 8)  # one pass: no scratch needed
+    torch.cuda.synchronize()
