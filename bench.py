@@ -559,9 +559,9 @@ def run_suite(args):
               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                            "algorithmic_bytes_per_step": 2 * cells},
               "cpu_baseline": cpu_leg(lambda: oracle.ca_step(gh), cells, "cells/s", "one step of the n = 16384 grid")})
-        # the same 100 steps through tri_ca_run: up to 8 steps per pass through
-        # memory (tiles read once with an 8-cell halo, stepped as bits in
-        # shared memory, written once), 13 passes
+        # the same 100 steps through tri_ca_run: up to 16 steps per pass through
+        # memory (one warp per tile: read once with a 16-cell halo, stepped as
+        # bits in registers, written once), 7 passes
         c = torch.zeros_like(a)
 
         def run100(m):
@@ -570,16 +570,16 @@ def run_suite(args):
             return go
         tr = {nm: graph_ms(run100(m), 1) for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB),
                                                         ("rb", tri.MAP_RB), ("rec", tri.MAP_REC))}
-        passes = -(-100 // 8)
+        passes = -(-100 // 16)
         gbs_run = 2.0 * cells * passes / (tr["lambda"] * 1e-3) / 1e9
         emit({"row": "life_run", "metric": "cell updates/s", "unit": "cells/s",
               "value": 100 * cells / (tr["lambda"] * 1e-3),
-              "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 32, "steps_per_pass": 8},
+              "config": {"workload": "life_n16384_bernoulli05_100steps", "rho": 32, "steps_per_pass": 16},
               "ms_per_100_steps": tr, "I_bb_over_lambda": tr["bb"] / tr["lambda"],
               "speedup_over_step_by_step": 100 * t["lambda"] / tr["lambda"],
               "roofline": {"bound": "hbm", "achieved": gbs_run, "peak": hbm, "unit": "GB/s", "frac": gbs_run / hbm,
                            "algorithmic_bytes_per_pass": 2 * cells, "passes": passes,
-                           "note": "one read and one write of every cell per pass; the 8-cell halos are re-read"}})
+                           "note": "one read and one write of every cell per pass; the 16-cell halos are re-read"}})
 
     if want("at"):
         # a7: Axilrod-Teller energy over the tetrahedral domain, N = 1536, rho = 16
@@ -785,7 +785,7 @@ def run_split(args, rank: int, world: int, local: int):
 def run_profile_case(args):
     """A few launches of one kernel on its small case, for ncu captures
     (select the launch with -k and -s / -c): the Life step (n = 16384,
-    lambda, rho 32), the AT energy (N = 1536, table map, rho 32), the FP32
+    lambda, rho 32), 32 Life steps through tri_ca_run (two passes, twice), the AT energy (N = 1536, table map, rho 32), the FP32
     EDM (N = 16384, d = 64, lambda, rho 16 x 8 x 8 pairs), the batched EDM
     (100 of the seeded instances, d = 64, rho 16 x 8 x 8) and the collision
     test (16384 spheres in 3-D, rho 16 x 8 x 8).  Four launches each."""
@@ -801,6 +801,12 @@ def run_profile_case(args):
         for _ in range(4):
             tri.tri_ca_step(a, b, n, map=tri.MAP_LAMBDA, rho=32)
             a, b = b, a
+    elif case == "life_run":
+        n = 16384
+        a = torch.from_numpy(inputs.ca_grid(n, seed=1609)).to(dev)
+        b, c = torch.zeros_like(a), torch.zeros_like(a)
+        for _ in range(2):
+            tri.tri_ca_run(a, b, n, 32, scratch=c, map=tri.MAP_LAMBDA, rho=32)  # two passes each
     elif case == "at":
         p = torch.from_numpy(inputs.at_points(1536, seed=1610)).to(dev)
         e = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -858,7 +864,7 @@ def main():
     ap.add_argument("--suite", action="store_true", help="one JSON line per other hot-path row instead")
     ap.add_argument("--only", default="", help="suite sections to run (maps,edm,life,at,collide,batched)")
     ap.add_argument("--collide-n", type=int, default=65536, help="spheres in the collision rows")
-    ap.add_argument("--profile", default="", choices=["", "life", "at", "edm", "batched", "collide"],
+    ap.add_argument("--profile", default="", choices=["", "life", "life_run", "at", "edm", "batched", "collide"],
                     help="run a few launches of one kernel's small case (for ncu captures) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -353,15 +353,15 @@ TRI_API int tri_ca_step(const uint8_t *in, uint8_t *out, uint32_t n, size_t ld,
 /*
  * tri_ca_run -- `steps` synchronous steps of the automaton of tri_ca_step,
  * the result in `out`.  Conway's rule at rho = 32 (128 x 128-cell tiles) runs
- * several steps per pass through memory: each block reads its tile with an
- * 8-cell halo once, as bits in shared memory, takes up to 8 steps there
+ * up to 16 steps per pass through memory: one warp per tile reads the tile
+ * with a 16-cell halo once, holds it as bits in registers (five region rows
+ * per lane, vertical neighbours by warp shuffle), takes the steps there
  * (clearing the cells outside the domain after each) and writes the tile's
- * domain cells once, so a pass costs about what one step of tri_ca_step
- * costs.  Other rules and rho take one tri_ca_step per step.  The result is
- * the same bit for bit as `steps` calls of tri_ca_step.
+ * domain cells once.  Other rules and rho take one tri_ca_step per step.  The
+ * result is the same bit for bit as `steps` calls of tri_ca_step.
  *   in (read only), out and scratch (device uint8, 16-byte aligned, row-major
  *   with leading dimension ld as in tri_ca_step): pairwise disjoint.  scratch
- *   holds intermediate states when more than one pass is needed (steps > 8
+ *   holds intermediate states when more than one pass is needed (steps > 16
  *   for the fused form, steps > 1 otherwise) and may be NULL otherwise.  Only
  *   domain cells of out and scratch are written.
  *   map: LAMBDA, LAMBDA_PDELTA, BB, RB or REC; rho in {8,16,32}; steps >= 1.

@@ -1,11 +1,12 @@
 // Several steps of Conway's rule per pass through memory (temporal blocking)
 // on the triangular domain {0 <= j <= i < n}.  Each block owns a 128 x 128
 // cell tile placed by a block map (Section 3; the triangular-domain automaton
-// of Section 1).  It reads the tile with a halo of K cells on every side,
-// once, as bits (32 cells per word) in shared memory, runs up to K steps
-// there, and writes the tile's domain cells back as bytes.  A cell of the
-// region is exact after s steps when it lies at least s cells inside the
-// region, so after K steps the tile itself is; the halo cells are computed
+// of Section 1).  One warp reads the tile with a halo of 16 cells on every
+// side, once, packs it to bits (32 cells per word) and keeps it in registers:
+// lane l holds region rows 5 l .. 5 l + 4, five words each.  It takes up to
+// 16 steps there and writes the tile's domain cells back as bytes.  A cell of
+// the region is exact after s steps when it lies at least s cells inside the
+// region, so after 16 steps the tile itself is; the halo cells are computed
 // only to get it there.  After every step the cells outside the domain
 // (j > i, i >= n, j < 0) are cleared, as the rule counts them dead.
 #include <cuda_runtime.h>
@@ -19,159 +20,244 @@ using namespace tri;
 
 namespace {
 
-constexpr uint32_t TS = 128;  // tile side in cells (the rho = 32 tile of tri_ca_step)
-constexpr uint32_t WPR = 5;   // words per region row: columns j0 - 16 .. j0 + 143 (halo <= 16)
-constexpr uint32_t PITCH = WPR + 2;  // a zero word on each side of a row in shared memory
-constexpr uint32_t GROUPS = 48;      // row groups: thread (w, g) steps word w of rows [g R, (g + 1) R)
-constexpr int RUN_THREADS = WPR * GROUPS;
+constexpr uint32_t TS = 128;                 // tile side in cells (the rho = 32 tile of tri_ca_step)
+constexpr int KH = 16;                       // halo in cells on each side, and steps per pass
+constexpr uint32_t WPR = 5;                  // words per region row: columns j0 - 16 .. j0 + 143
+constexpr uint32_t ROWS = TS + 2 * KH;       // region rows: i0 - 16 .. i0 + 143
+constexpr uint32_t RPL = ROWS / 32;          // region rows per lane
+static_assert(RPL * 32 == ROWS, "one warp holds the region");
+static_assert(KH <= 16, "the halo must fit the 16-cell margins of the region's words");
 
-// byte k of x non-zero -> bit k (k < 4): bit 7 of each byte marks a non-zero
-// byte (its low seven bits plus 0x7F carry into bit 7 unless all zero); one
-// multiply then moves the four marks, 8 bits apart, to bits 24 .. 27.
-__device__ __forceinline__ uint32_t bytes4_to_bits(uint32_t x)
+// Four bytes -> four bits at 0 .. 3 (byte k non-zero -> bit k).  Bit 7 of
+// each byte of t marks a non-zero byte: its low seven bits plus 0x7F carry
+// into bit 7 unless all zero, and a byte >= 0x80 has it already.  Times
+// 2^21 + 2^14 + 2^7 + 1, bits 7, 15, 23, 31 land at 28, 29, 30, 31; every
+// other product bit lands below 28 or past 31, each at its own position, so
+// nothing carries into the top four.
+__device__ __forceinline__ uint32_t nib_of(uint32_t x)
 {
     const uint32_t t = (((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
-    return ((t >> 7) * 0x01020408u) >> 24;
+    return (t * 0x00204081u) >> 28;
+}
+
+// 16 bytes -> 16 bits
+__device__ __forceinline__ uint32_t pack16(const uint4 q)
+{
+    return nib_of(q.x) + 16u * (nib_of(q.y) + 16u * (nib_of(q.z) + 16u * nib_of(q.w)));
 }
 
 // bit k of a nibble -> byte k = 0 or 1: the multiply puts copies of bit k at
 // k, k + 7, k + 14, k + 21, and only the copy at 8k falls on a byte's bit 0.
 __device__ __forceinline__ uint32_t bits4_to_bytes(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
 
-// One row's three neighbour planes of word w: west (column b - 1), the word
-// itself and east (column b + 1), from the words left (l) and right (r) of it.
-struct Planes {
-    uint32_t w, c, e;
+// bits lo .. hi of a word (empty when hi < lo), for any ints
+__device__ __forceinline__ uint32_t span_bits(int lo, int hi)
+{
+    lo = lo > 0 ? lo : 0;
+    hi = hi < 31 ? hi : 31;
+    if (hi < lo) return 0u;
+    return (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
+}
+
+__device__ __forceinline__ int clamp_small(int64_t v) { return (int)(v < -4096 ? -4096 : (v > 4096 ? 4096 : v)); }
+
+// The domain within the region as small ints: region rows g in [ilo, ihi]
+// are cell rows 0 .. n - 1, and row g holds the domain's region columns lo ..
+// min(dd + g, lastrel) (dd = i0 - j0; lastrel = n - 1 - (j0 - 16); lo = 16
+// in the first block column, where cell column 0 is region column 16).
+// Values beyond +-4096 are clamped: only -1 .. 160 matter.
+struct RegionDomain {
+    int lo, dd, lastrel, ilo, ihi;
+    __device__ __forceinline__ uint32_t mask(int g, int w) const
+    {
+        if (g < ilo || g > ihi) return 0u;
+        const int hi = min(dd + g, lastrel);
+        return span_bits(lo - 32 * w, hi - 32 * w);
+    }
+    // every cell of the region lies in the domain
+    __device__ __forceinline__ bool full() const
+    {
+        return lo == 0 && ilo == 0 && ihi >= (int)ROWS - 1 && dd >= (int)ROWS - 1 && lastrel >= (int)ROWS - 1;
+    }
 };
-__device__ __forceinline__ Planes planes(uint32_t l, uint32_t c, uint32_t r)
+
+// For each word of a row: the sum of the cell and its two side neighbours as
+// (s3 + 2 c3), and of the two side neighbours alone as (s2 + 2 c2), from the
+// row's west and east planes (bit b of a word is region column 32 w + b).
+__device__ __forceinline__ void row_sums(const uint32_t (&row)[WPR], uint32_t (&s3)[WPR], uint32_t (&c3)[WPR],
+                                         uint32_t (&s2)[WPR], uint32_t (&c2)[WPR])
 {
-    return {__funnelshift_l(l, c, 1), c, __funnelshift_r(c, r, 1)};
+#pragma unroll
+    for (uint32_t w = 0; w < WPR; ++w) {
+        const uint32_t l = w ? row[w - 1] : 0u, r = w + 1 < WPR ? row[w + 1] : 0u;
+        const uint32_t W = __funnelshift_l(l, row[w], 1), E = __funnelshift_r(row[w], r, 1);
+        s2[w] = W ^ E;
+        c2[w] = W & E;
+        s3[w] = s2[w] ^ row[w];
+        c3[w] = c2[w] | (row[w] & s2[w]);
+    }
 }
 
-// One step of Conway's rule for 32 cells from the planes of the row above
-// (u), the row itself (m) and the row below (d).
-__device__ __forceinline__ uint32_t life_word(const Planes &u, const Planes &m, const Planes &d)
+// `steps` steps of the region held by the warp.  Each lane gets the row
+// above its first and below its last from its neighbours by shuffle; each
+// row's sums are formed once and used by the rows above and below it.  The
+// region's first and last rows are stepped from whatever their shuffles
+// return: like every cell that lacks neighbours in the region, they are
+// wrong after the first step, and the wrong rim grows one cell per step.
+template <bool MASKED>
+__device__ __forceinline__ void run_steps(uint32_t (&c)[RPL][WPR], uint32_t lane, uint32_t steps,
+                                          const RegionDomain &dom)
 {
-    // row sums as (ones, twos): three cells above, three below, two beside
-    const uint32_t sa = u.w ^ u.c ^ u.e, ca = (u.w & u.c) | (u.e & (u.w ^ u.c));
-    const uint32_t sb = d.w ^ d.c ^ d.e, cb = (d.w & d.c) | (d.e & (d.w ^ d.c));
-    const uint32_t sm = m.w ^ m.e, cm = m.w & m.e;
-    // count = x1 + 2 (x2 + y1) + 4 y2 = x1 + 2 z1 + 4 (z2 + y2)
-    const uint32_t x1 = sa ^ sb ^ sm, x2 = (sa & sb) | (sm & (sa ^ sb));
-    const uint32_t y1 = ca ^ cb ^ cm, y2 = (ca & cb) | (cm & (ca ^ cb));
-    const uint32_t z1 = x2 ^ y1, z2 = x2 & y1;
-    // alive next: count 3, or count 2 and alive now (count >= 4 when z2 | y2)
-    return z1 & ~(z2 | y2) & (x1 | m.c);
+    for (uint32_t s = 0; s < steps; ++s) {
+        uint32_t up[WPR], dn[WPR];
+#pragma unroll
+        for (uint32_t w = 0; w < WPR; ++w) {
+            up[w] = __shfl_up_sync(0xFFFFFFFFu, c[RPL - 1][w], 1);
+            dn[w] = __shfl_down_sync(0xFFFFFFFFu, c[0][w], 1);
+        }
+        uint32_t ps3[WPR], pc3[WPR], cs3[WPR], cc3[WPR], cs2[WPR], cc2[WPR], t2[WPR], u2[WPR];
+        row_sums(up, ps3, pc3, t2, u2);
+        row_sums(c[0], cs3, cc3, cs2, cc2);
+#pragma unroll
+        for (uint32_t r = 0; r < RPL; ++r) {
+            uint32_t ns3[WPR], nc3[WPR], ns2[WPR], nc2[WPR];
+            if (r + 1 < RPL)
+                row_sums(c[r + 1], ns3, nc3, ns2, nc2);
+            else
+                row_sums(dn, ns3, nc3, ns2, nc2);
+#pragma unroll
+            for (uint32_t w = 0; w < WPR; ++w) {
+                // the 8 neighbours: (ps3 + 2 pc3) + (ns3 + 2 nc3) + (cs2 + 2 cc2)
+                // = x1 + 2 (x2 + y1) + 4 y2
+                const uint32_t x1 = ps3[w] ^ ns3[w] ^ cs2[w];
+                const uint32_t x2 = (ps3[w] & ns3[w]) | (cs2[w] & (ps3[w] ^ ns3[w]));
+                const uint32_t y1 = pc3[w] ^ nc3[w] ^ cc2[w];
+                const uint32_t y2 = (pc3[w] & nc3[w]) | (cc2[w] & (pc3[w] ^ nc3[w]));
+                // alive next: count 3, or count 2 and alive now (>= 4 when x2 & y1 or y2)
+                uint32_t v = (x2 ^ y1) & ~((x2 & y1) | y2) & (x1 | c[r][w]);
+                if constexpr (MASKED) v &= dom.mask((int)(lane * RPL + r), (int)w);
+                c[r][w] = v;
+            }
+#pragma unroll
+            for (uint32_t w = 0; w < WPR; ++w) {
+                ps3[w] = cs3[w];
+                pc3[w] = cc3[w];
+                cs3[w] = ns3[w];
+                cc3[w] = nc3[w];
+                cs2[w] = ns2[w];
+                cc2[w] = nc2[w];
+            }
+        }
+    }
 }
 
-template <int MAP, int K>
-__global__ void __launch_bounds__(RUN_THREADS) ca_life_run_kernel(const uint8_t *__restrict__ in,
-                                                                   uint8_t *__restrict__ out, uint32_t n, size_t ld,
-                                                                   BlockMap bm, uint32_t steps)
+// 128 registers a thread (16 warps per SM): the ALU pipe, not occupancy,
+// bounds the steps
+template <int MAP>
+__global__ void __launch_bounds__(32, 16) ca_life_run_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
+                                                             uint32_t n, size_t ld, BlockMap bm, uint32_t steps)
 {
-    static_assert(K >= 1 && K <= 16, "the halo must fit the 16-cell margins of the region's words");
     uint32_t bi, bj;
     if (!map_block<MAP>(bm, bi, bj)) return;
-    constexpr uint32_t ROWS = TS + 2 * K, RPT = (ROWS + GROUPS - 1) / GROUPS;
-    // the state (two buffers, rows of PITCH words: a zero, words 0 .. 4, a
-    // zero) and the domain mask; region row r = cell row i0 - K + r, bit b of
-    // word w = column j0 - 16 + 32 w + b
-    __shared__ uint32_t s_a[ROWS * PITCH], s_b[ROWS * PITCH], s_mask[ROWS * WPR];
-    const uint32_t tid = threadIdx.y * WPR + threadIdx.x;
+    __shared__ uint32_t s_rows[ROWS * WPR];  // region row g, word w at g * WPR + w
+    const uint32_t lane = threadIdx.x;
     const int64_t i0 = (int64_t)bi * TS, j0 = (int64_t)bj * TS;
-    const int64_t ibase = i0 - K, jbase = j0 - 16, last = (int64_t)n - 1;
+    const int64_t ibase = i0 - KH, jbase = j0 - 16, last = (int64_t)n - 1;
+    RegionDomain dom;
+    dom.lo = bj == 0 ? 16 : 0;
+    dom.dd = clamp_small(i0 - j0);
+    dom.lastrel = clamp_small(last - jbase);
+    dom.ilo = clamp_small(ibase < 0 ? -ibase : 0);
+    dom.ihi = clamp_small(last - ibase);
+    const bool full = dom.full();
 
-    for (uint32_t e = tid; e < ROWS * WPR; e += RUN_THREADS) {
-        const uint32_t r = e / WPR, w = e - r * WPR;
-        const int64_t i = ibase + r, c0 = jbase + 32 * (int64_t)w;
-        // domain columns of the word: 0 <= c0 + b <= min(i, n - 1), for 0 <= i < n
-        uint32_t mask = 0;
-        if (i >= 0 && i <= last) {
-            const int64_t lo = -c0 > 0 ? -c0 : 0;
-            const int64_t top = (i < last ? i : last) - c0, hi = top < 31 ? top : 31;
-            if (hi >= lo) mask = (hi - lo == 31) ? 0xFFFFFFFFu : (((1u << (hi - lo + 1)) - 1u) << lo);
-        }
-        uint32_t bits = 0;
-        // a half word with a domain column starts at a column in [0, n - 1]:
-        // its 16-byte chunk lies inside the row (ld >= n, both multiples of 16)
+    // load: region word e = g * WPR + w, five words a lane at a time, every
+    // load of a batch issued before any is used; a tile whose region lies
+    // inside the domain needs no masks
+#pragma unroll 1
+    for (uint32_t b = 0; b < ROWS * WPR / 32; b += 5) {
+        uint4 v[5][2];
+        uint32_t mk[5];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if ((mask >> (16 * h)) & 0xFFFFu) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(in + (size_t)i * ld + (size_t)(c0 + 16 * h));
-                const uint32_t b16 = bytes4_to_bits(v.x) | (bytes4_to_bits(v.y) << 4) |
-                                     (bytes4_to_bits(v.z) << 8) | (bytes4_to_bits(v.w) << 12);
-                bits |= b16 << (16 * h);
+        for (uint32_t k = 0; k < 5; ++k) {
+            const uint32_t e = (b + k) * 32 + lane, g = e / WPR, w = e - g * WPR;
+            if (full) {
+                const uint8_t *src = in + (size_t)(ibase + g) * ld + (size_t)(jbase + 32 * (int64_t)w);
+                mk[k] = 0xFFFFFFFFu;
+                v[k][0] = *reinterpret_cast<const uint4 *>(src);
+                v[k][1] = *reinterpret_cast<const uint4 *>(src + 16);
+            } else {
+                mk[k] = dom.mask((int)g, (int)w);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    // a half word with a domain column starts at a column in [0, n - 1]:
+                    // its 16-byte chunk lies inside the row (ld >= n, both multiples of 16)
+                    v[k][h] = make_uint4(0, 0, 0, 0);
+                    if ((mk[k] >> (16 * h)) & 0xFFFFu)
+                        v[k][h] = *reinterpret_cast<const uint4 *>(in + (size_t)(ibase + g) * ld +
+                                                                   (size_t)(jbase + 32 * (int64_t)w + 16 * h));
+                }
             }
         }
-        s_a[r * PITCH + 1 + w] = bits & mask;
-        // the first and last region rows are never stepped: both buffers keep them
-        if (r == 0 || r == ROWS - 1) s_b[r * PITCH + 1 + w] = bits & mask;
-        s_mask[e] = mask;
+#pragma unroll
+        for (uint32_t k = 0; k < 5; ++k)
+            s_rows[(b + k) * 32 + lane] = (pack16(v[k][0]) + 65536u * pack16(v[k][1])) & mk[k];
     }
-    for (uint32_t r = tid; r < ROWS; r += RUN_THREADS) {
-        s_a[r * PITCH] = s_a[r * PITCH + PITCH - 1] = 0u;
-        s_b[r * PITCH] = s_b[r * PITCH + PITCH - 1] = 0u;
-    }
-    __syncthreads();
+    __syncwarp();
+    // lane l takes region rows 5 l .. 5 l + 4 (a stride of 25 words: no bank conflicts)
+    uint32_t c[RPL][WPR];
+#pragma unroll
+    for (uint32_t r = 0; r < RPL; ++r)
+#pragma unroll
+        for (uint32_t w = 0; w < WPR; ++w) c[r][w] = s_rows[(lane * RPL + r) * WPR + w];
+    if (full)
+        run_steps<false>(c, lane, steps, dom);
+    else
+        run_steps<true>(c, lane, steps, dom);
+    __syncwarp();
+#pragma unroll
+    for (uint32_t r = 0; r < RPL; ++r)
+#pragma unroll
+        for (uint32_t w = 0; w < WPR; ++w) s_rows[(lane * RPL + r) * WPR + w] = c[r][w];
+    __syncwarp();
 
-    // thread (w, g) steps word w of rows r0 .. r1 - 1, sliding a window of
-    // three rows down them; the first and last region rows have no row
-    // beyond them and keep their first values, which reach at most K - 1
-    // rows inward in K steps
-    const uint32_t w = threadIdx.x;
-    const uint32_t r0 = max(1u, threadIdx.y * RPT), r1 = min(ROWS - 1, (threadIdx.y + 1) * RPT);
-    uint32_t *cur = s_a, *nxt = s_b;
-    for (uint32_t s = 0; s < steps; ++s) {
-        if (r0 < r1) {
-            const uint32_t *p = cur + (r0 - 1) * PITCH + w;  // words w - 1 .. w + 1 at p[0 .. 2]
-            Planes up = planes(p[0], p[1], p[2]);
-            Planes mid = planes(p[PITCH], p[PITCH + 1], p[PITCH + 2]);
-            for (uint32_t r = r0; r < r1; ++r) {
-                const uint32_t *q = cur + (r + 1) * PITCH + w;
-                const Planes dn = planes(q[0], q[1], q[2]);
-                nxt[r * PITCH + 1 + w] = life_word(up, mid, dn) & s_mask[r * WPR + w];
-                up = mid;
-                mid = dn;
-            }
-        }
-        __syncthreads();
-        uint32_t *t = cur;
-        cur = nxt;
-        nxt = t;
-    }
-
-    // the tile's domain cells: 128 rows x 8 chunks of 16 cells; chunk ch is
-    // region bits 16 + 16 ch .. +15, inside one word (shift 0 or 16)
-    for (uint32_t e = tid; e < TS * 8; e += RUN_THREADS) {
+    // the tile's domain cells: 128 rows x 8 chunks of 16 cells; chunk ch of
+    // tile row rr is bits 16 + 16 ch .. + 15 of region row KH + rr (all of
+    // them for a tile inside the domain)
+#pragma unroll 4
+    for (uint32_t e = lane; e < TS * 8; e += 32) {
         const uint32_t rr = e >> 3, ch = e & 7;
-        const int64_t i = i0 + rr, c = j0 + 16 * (int64_t)ch;
-        if (i > last || c > i) continue;
+        const int64_t i = i0 + rr, col = j0 + 16 * (int64_t)ch;
         const uint32_t off = 16 + 16 * ch;
-        const uint32_t b16 = (cur[(K + rr) * PITCH + 1 + (off >> 5)] >> (off & 31)) & 0xFFFFu;
-        uint8_t *dst = out + (size_t)i * ld + (size_t)c;
+        const uint32_t b16 = s_rows[(KH + rr) * WPR + (off >> 5)] >> (off & 31);
+        const uint4 q = make_uint4(bits4_to_bytes(b16 & 15u), bits4_to_bytes((b16 >> 4) & 15u),
+                                   bits4_to_bytes((b16 >> 8) & 15u), bits4_to_bytes((b16 >> 12) & 15u));
+        if (full) {
+            *reinterpret_cast<uint4 *>(out + (size_t)i * ld + (size_t)col) = q;
+            continue;
+        }
+        if (i > last || col > i) continue;
+        uint8_t *dst = out + (size_t)i * ld + (size_t)col;
         const int64_t lastc = i < last ? i : last;  // the row's last domain column
-        if (c + 15 <= lastc) {
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(bits4_to_bytes(b16 & 15u), bits4_to_bytes((b16 >> 4) & 15u),
-                                                         bits4_to_bytes((b16 >> 8) & 15u), bits4_to_bytes(b16 >> 12));
+        if (col + 15 <= lastc) {
+            *reinterpret_cast<uint4 *>(dst) = q;
         } else {
-            for (int64_t k = 0; k <= lastc - c; ++k) dst[k] = (uint8_t)((b16 >> k) & 1u);
+            for (int64_t k = 0; k <= lastc - col; ++k) dst[k] = (uint8_t)((b16 >> k) & 1u);
         }
     }
 }
 
-template <int K>
 int launch_run_pass(int map, const uint8_t *in, uint8_t *out, uint32_t n, size_t ld, uint32_t steps, cudaStream_t s)
 {
     const uint32_t m = (n + TS - 1) / TS;
     return trihost::map_launches(map, m, [&](auto tag, dim3 g, const BlockMap &bm) -> cudaError_t {
         constexpr int MAP = decltype(tag)::value;
-        ca_life_run_kernel<MAP, K><<<g, dim3(WPR, GROUPS), 0, s>>>(in, out, n, ld, bm, steps);
+        ca_life_run_kernel<MAP><<<g, 32, 0, s>>>(in, out, n, ld, bm, steps);
         return cudaGetLastError();
     });
 }
 
 constexpr uint32_t LIFE_BIRTH_MASK = 1u << 3, LIFE_SURVIVE_MASK = (1u << 2) | (1u << 3);
-constexpr uint32_t RUN_K = 8;  // steps per pass
 
 bool overlap(const uint8_t *a, const uint8_t *b, size_t span) { return a < b + span && b < a + span; }
 
@@ -189,7 +275,7 @@ extern "C" int tri_ca_run(const uint8_t *in, uint8_t *out, uint8_t *scratch, uin
         map != TRI_MAP_REC)
         return TRI_EINVAL;
     const bool fused = birth_mask == LIFE_BIRTH_MASK && survive_mask == LIFE_SURVIVE_MASK && rho == 32;
-    const uint32_t per = fused ? RUN_K : 1u;
+    const uint32_t per = fused ? (uint32_t)KH : 1u;
     const uint32_t passes = (steps + per - 1) / per;
     const size_t span = (size_t)(n - 1) * ld + n;
     if (overlap(in, out, span)) return TRI_EINVAL;
@@ -205,7 +291,7 @@ extern "C" int tri_ca_run(const uint8_t *in, uint8_t *out, uint8_t *scratch, uin
         const uint32_t k = std::min(per, steps - p * per);
         int r;
         if (fused)
-            r = launch_run_pass<RUN_K>(map, src, dst, n, ld, k, s);
+            r = launch_run_pass(map, src, dst, n, ld, k, s);
         else
             r = tri_ca_step(src, dst, n, ld, birth_mask, survive_mask, map, rho, stream);
         if (r != TRI_OK) return r;

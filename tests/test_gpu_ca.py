@@ -103,7 +103,7 @@ def test_ca_n16384_hundred_steps(orc):
     for m in (t.MAP_LAMBDA, t.MAP_BB):
         got = _run(t, g, n, 100, m, 32)
         assert np.array_equal(got, ref), m
-        # the same 100 steps in passes of up to 8 steps (tri_ca_run)
+        # the same 100 steps in passes of up to 16 steps (tri_ca_run)
         assert np.array_equal(_run_fused(t, g, n, 100, m, 32), ref), ("run", m)
 
 
@@ -124,12 +124,13 @@ def _run_fused(t, g, n, steps, map_id, rho, birth=None, survive=None):
 
 @pytest.mark.parametrize("mapname", ["LAMBDA", "LAMBDA_PDELTA", "BB", "RB", "REC"])
 def test_ca_run_fused_matches_the_oracle(orc, mapname):
-    # Conway's rule at rho = 32 runs up to 8 steps per pass: step counts below,
-    # at and across a pass, sizes around the 128-cell tile, a padded leading
+    # Conway's rule at rho = 32 runs up to 16 steps per pass: step counts below,
+    # at and across a pass, sizes around the 128-cell tile and sizes with tiles
+    # whose 16-cell halo lies wholly inside the domain (n >= 1000), a padded leading
     # dimension and junk above the diagonal (outside the domain)
     t = tri()
     map_id = getattr(t, "MAP_" + mapname)
-    for n in (1, 5, 127, 128, 129, 300, 1000, 1024):
+    for n in (1, 5, 127, 128, 129, 300, 1000, 1024, 2500):
         m = -(-n // 128)
         if mapname == "REC" and m & (m - 1):
             continue
@@ -137,9 +138,29 @@ def test_ca_run_fused_matches_the_oracle(orc, mapname):
         g = inputs.ca_grid(n, seed=n + 3, ld=ld)
         g[np.triu_indices(n, 1)] = 5
         g[:, n:] = 9
-        for steps in (1, 3, 8, 9, 17):
+        for steps in (1, 3, 8, 15, 16, 17, 33):
             got = _run_fused(t, g, n, steps, map_id, 32)
             assert np.array_equal(got, orc.ca_run(g, steps)), (mapname, n, steps)
+
+
+def test_ca_run_any_nonzero_byte_is_alive(orc):
+    # a cell is alive when its byte is non-zero: live cells carry bytes with
+    # every bit pattern that the byte-to-bit packing must map to 1 (0x01, 0x7F,
+    # 0x80, 0x81, 0xFF and random ones), in tiles inside the domain and on its
+    # edges, for one step, one pass and across passes
+    t = tri()
+    rng = np.random.default_rng(1609)
+    for n in (300, 1000):
+        g = inputs.ca_grid(n, seed=n + 11, ld=-(-n // 16) * 16)
+        live = g != 0
+        vals = rng.choice(np.array([0x01, 0x7F, 0x80, 0x81, 0xFF, 0x10, 0x02, 0x40], dtype=np.uint8), size=g.shape)
+        rnd = rng.integers(1, 256, size=g.shape, dtype=np.uint8)
+        vals = np.where(rng.random(g.shape) < 0.5, vals, rnd)
+        g = np.where(live, vals, 0).astype(np.uint8)
+        for map_id in (t.MAP_LAMBDA, t.MAP_BB):
+            for steps in (1, 16, 17):
+                got = _run_fused(t, g, n, steps, map_id, 32)
+                assert np.array_equal(got, orc.ca_run(g, steps)), (n, map_id, steps)
 
 
 def test_ca_run_other_rules_and_tiles(orc):
@@ -161,7 +182,7 @@ def test_ca_run_errors():
     n = 200
     a = torch.zeros((n, 208), dtype=torch.uint8, device=dev())
     b, c = torch.zeros_like(a), torch.zeros_like(a)
-    cases = [dict(steps=0, scratch=c), dict(steps=9, scratch=None), dict(steps=9, scratch=a),
+    cases = [dict(steps=0, scratch=c), dict(steps=17, scratch=None), dict(steps=17, scratch=a),
              dict(steps=3, scratch=c, map=t.MAP_UTM)]
     for kw in cases:
         with pytest.raises(t.TriError) as e:
@@ -170,5 +191,5 @@ def test_ca_run_errors():
     with pytest.raises(t.TriError) as e:
         t.tri_ca_run(a, a, n, 3)  # out is in
     assert e.value.status == t.TRI_EINVAL
-    t.tri_ca_run(a, b, n, 8)  # one pass: no scratch needed
+    t.tri_ca_run(a, b, n, 16)  # one pass: no scratch needed
     torch.cuda.synchronize()
