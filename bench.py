@@ -275,7 +275,7 @@ def paper_comparison(tri, inputs, dev, stream):
     (Section 5) of lambda, the bounding box and the rectangular box on the
     paper-size EDM (N = 2048, d = 3, one pair per thread, rho = 16, as the
     paper launches it) and on one triangular Life step (n = 16384, rho = 32);
-    the Axilrod-Teller energy under the tetrahedral maps; and the 1000-instance
+    the Life workload's 100 steps through tri_ca_run; the Axilrod-Teller energy under the tetrahedral maps; and the 1000-instance
     batched EDM against separate launches.  I = t_BB / t_map."""
     import torch
     out = {}
@@ -297,7 +297,14 @@ def paper_comparison(tri, inputs, dev, stream):
     t = {nm: graph_time_ms(life(m), 1, stream) / 10
          for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB))}
     out["life_n16384_step_rho32"] = {"ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()}}
-    del x, o, a, b
+    # the Life workload as configured, 100 steps, through tri_ca_run (up to 16
+    # steps per pass through memory)
+    c = torch.zeros_like(a)
+    t = {nm: graph_time_ms(lambda: tri.tri_ca_run(a, b, n, 100, scratch=c, map=m, rho=32), 1, stream)
+         for nm, m in (("lambda", tri.MAP_LAMBDA), ("bb", tri.MAP_BB), ("rb", tri.MAP_RB))}
+    out["life_n16384_100steps_run"] = {"ms": t, "I_bb_over": {k: t["bb"] / v for k, v in t.items()},
+                                       "cell_updates_per_s": 100 * (n * (n + 1) // 2) / (t["lambda"] * 1e-3)}
+    del x, o, a, b, c
     # the Axilrod-Teller energy over the tetrahedral domain (Section 6), N = 1536, rho = 32:
     # the cubic-root map, the table of layer starts (Section 7) and the m^3 box
     pts = torch.from_numpy(inputs.at_points(1536, seed=1610)).to(dev)

@@ -38,8 +38,8 @@ def test_headline_line_keys():
     assert d["e2e"]["d2h_bytes_per_step"] == 4 * 4096 * 4097 // 2
     for k in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert k in d["clocks"], k
-    assert set(d["paper_maps"]) >= {"edm_n2048_d3_rho16_reg1", "life_n16384_step_rho32", "at_energy_n1536_rho32",
-                                    "edm_batched_1000_d64"}
+    assert set(d["paper_maps"]) >= {"edm_n2048_d3_rho16_reg1", "life_n16384_step_rho32", "life_n16384_100steps_run",
+                                    "at_energy_n1536_rho32", "edm_batched_1000_d64"}
 
 
 def test_split_at_one_rank():
