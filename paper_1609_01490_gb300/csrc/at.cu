@@ -96,7 +96,7 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
         }
         const uint32_t kend = min(j, (C + 1) * rho) - C * rho;  // k < j
         const float *brow = sb[threadIdx.x];
-        const f2 K = f2_pack(0.375f, 0.375f), ONE = f2_pack(1.0f, 1.0f);
+        const f2 K = f2_pack(0.375f, 0.375f), ONE = f2_pack(1.0f, 1.0f), M2 = f2_pack(-2.0f, -2.0f);
         uint32_t t = 0;
         for (; t + 1 < kend; t += 2) {
             const f2 b = *reinterpret_cast<const f2 *>(&brow[t]);
@@ -104,13 +104,15 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
             for (int u = 0; u < AT_ROWS; ++u) {
                 const f2 c = *reinterpret_cast<const f2 *>(&crow[u][t]);
                 const f2 q = f2_mul(f2_mul(A[u], b), c);
-                const f2 P = f2_mul(f2_mul(f2_sub(f2_add(A[u], c), b), f2_sub(f2_add(A[u], b), c)),
-                                    f2_sub(f2_add(b, c), A[u]));
+                // P = (b + c - a)(c + a - b)(a + b - c) = (s - 2a)(s - 2b)(s - 2c), s = a + b + c
+                const f2 sum = f2_add(f2_add(A[u], b), c);
+                const f2 P = f2_mul(f2_mul(f2_fma(M2, A[u], sum), f2_fma(M2, b, sum)), f2_fma(M2, c, sum));
                 float q0, q1;
                 f2_unpack(q, q0, q1);
                 const f2 rs = f2_pack(rsqrtf(q0), rsqrtf(q1));
                 const f2 inv = f2_mul(rs, rs);
-                S[u] = f2_add(S[u], f2_mul(f2_mul(f2_fma(f2_mul(K, P), inv, ONE), inv), rs));
+                // term = (1 + 3 P / (8 q)) / q^(3/2), accumulated by one fused multiply-add
+                S[u] = f2_fma(f2_mul(f2_fma(f2_mul(K, P), inv, ONE), inv), rs, S[u]);
             }
         }
 #pragma unroll
@@ -121,10 +123,11 @@ __global__ void at_kernel(const float *__restrict__ p, uint32_t n, double nu, ui
             if (t < kend) {  // an odd last k
                 const float a = a1[u], b = brow[t], c = crow[u][t];
                 const float q = a * b * c;
-                const float P = (a + c - b) * (a + b - c) * (b + c - a);
+                const float sum = a + b + c;
+                const float P = fmaf(-2.0f, a, sum) * fmaf(-2.0f, b, sum) * fmaf(-2.0f, c, sum);
                 const float rs = rsqrtf(q);
                 const float inv = rs * rs;
-                su += fmaf(0.375f * P, inv, 1.0f) * inv * rs;
+                su = fmaf(fmaf(0.375f * P, inv, 1.0f) * inv, rs, su);
             }
             if (act[u]) s += su;
         }
