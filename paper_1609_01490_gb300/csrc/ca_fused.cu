@@ -98,33 +98,62 @@ __device__ __forceinline__ void row_sums(const uint32_t (&row)[WPR], uint32_t (&
     }
 }
 
-// `steps` steps of the region held by the warp.  Each lane gets the row
-// above its first and below its last from its neighbours by shuffle; each
-// row's sums are formed once and used by the rows above and below it.  The
-// region's first and last rows are stepped from whatever their shuffles
-// return: like every cell that lacks neighbours in the region, they are
-// wrong after the first step, and the wrong rim grows one cell per step.
+// `steps` steps of the region held by the warp.  Each row's sums are formed
+// once, by the lane that holds it, and used by the rows above and below it;
+// a lane gets the 3-sums of the row above its first and below its last from
+// its neighbours by shuffle.  The region's first and last rows are stepped
+// from whatever their shuffles return: like every cell that lacks neighbours
+// in the region, they are wrong after the first step, and the wrong rim grows
+// one cell per step.
 template <bool MASKED>
 __device__ __forceinline__ void run_steps(uint32_t (&c)[RPL][WPR], uint32_t lane, uint32_t steps,
                                           const RegionDomain &dom)
 {
     for (uint32_t s = 0; s < steps; ++s) {
-        uint32_t up[WPR], dn[WPR];
+        // sums of the lane's first and last rows, formed once: their 3-sums go
+        // to the neighbouring lanes by shuffle (as the sums of the row above
+        // or below theirs) and all four are used here
+        uint32_t fs3[WPR], fc3[WPR], fs2[WPR], fc2[WPR], ls3[WPR], lc3[WPR], ls2[WPR], lc2[WPR];
+        row_sums(c[0], fs3, fc3, fs2, fc2);
+        row_sums(c[RPL - 1], ls3, lc3, ls2, lc2);
+        uint32_t ps3[WPR], pc3[WPR], ds3[WPR], dc3[WPR];
 #pragma unroll
         for (uint32_t w = 0; w < WPR; ++w) {
-            up[w] = __shfl_up_sync(0xFFFFFFFFu, c[RPL - 1][w], 1);
-            dn[w] = __shfl_down_sync(0xFFFFFFFFu, c[0][w], 1);
+            ps3[w] = __shfl_up_sync(0xFFFFFFFFu, ls3[w], 1);
+            pc3[w] = __shfl_up_sync(0xFFFFFFFFu, lc3[w], 1);
+            ds3[w] = __shfl_down_sync(0xFFFFFFFFu, fs3[w], 1);
+            dc3[w] = __shfl_down_sync(0xFFFFFFFFu, fc3[w], 1);
         }
-        uint32_t ps3[WPR], pc3[WPR], cs3[WPR], cc3[WPR], cs2[WPR], cc2[WPR], t2[WPR], u2[WPR];
-        row_sums(up, ps3, pc3, t2, u2);
-        row_sums(c[0], cs3, cc3, cs2, cc2);
+        uint32_t cs3[WPR], cc3[WPR], cs2[WPR], cc2[WPR];
+#pragma unroll
+        for (uint32_t w = 0; w < WPR; ++w) {
+            cs3[w] = fs3[w];
+            cc3[w] = fc3[w];
+            cs2[w] = fs2[w];
+            cc2[w] = fc2[w];
+        }
 #pragma unroll
         for (uint32_t r = 0; r < RPL; ++r) {
             uint32_t ns3[WPR], nc3[WPR], ns2[WPR], nc2[WPR];
-            if (r + 1 < RPL)
+            if (r + 2 < RPL) {
                 row_sums(c[r + 1], ns3, nc3, ns2, nc2);
-            else
-                row_sums(dn, ns3, nc3, ns2, nc2);
+            } else if (r + 2 == RPL) {
+#pragma unroll
+                for (uint32_t w = 0; w < WPR; ++w) {
+                    ns3[w] = ls3[w];
+                    nc3[w] = lc3[w];
+                    ns2[w] = ls2[w];
+                    nc2[w] = lc2[w];
+                }
+            } else {  // the row below the lane's last: its 3-sums from the next lane
+#pragma unroll
+                for (uint32_t w = 0; w < WPR; ++w) {
+                    ns3[w] = ds3[w];
+                    nc3[w] = dc3[w];
+                    ns2[w] = 0u;
+                    nc2[w] = 0u;
+                }
+            }
 #pragma unroll
             for (uint32_t w = 0; w < WPR; ++w) {
                 // the 8 neighbours: (ps3 + 2 pc3) + (ns3 + 2 nc3) + (cs2 + 2 cc2)
@@ -151,8 +180,8 @@ __device__ __forceinline__ void run_steps(uint32_t (&c)[RPL][WPR], uint32_t lane
     }
 }
 
-// 128 registers a thread (16 warps per SM): the ALU pipe, not occupancy,
-// bounds the steps
+// 128 registers a thread (16 warps per SM; a few spill in the masked form):
+// the ALU pipe, not occupancy, bounds the steps
 template <int MAP>
 __global__ void __launch_bounds__(32, 16) ca_life_run_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
                                                              uint32_t n, size_t ld, BlockMap bm, uint32_t steps)
