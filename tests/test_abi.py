@@ -101,3 +101,34 @@ def test_host_side_argument_errors_of_the_later_calls(lib):
     L.tet_at_workspace_size.argtypes = [u32, u32, i32, ctypes.POINTER(ctypes.c_size_t)]
     n = ctypes.c_size_t(0)
     assert L.tet_at_workspace_size(96, 16, 6, ctypes.byref(n)) == 0 and n.value == 8 * (6 * 7 * 8 // 6)
+
+
+def test_host_side_argument_errors_of_tri_ca_run(lib):
+    # rejected on the host before any CUDA call: null or misaligned buffers, a
+    # leading dimension below n or not a multiple of 16, steps = 0, rule masks
+    # past 8 neighbours, a map without a 2-D block grid, overlapping buffers and
+    # a missing scratch when more than one pass is needed (over 16 steps for
+    # Conway's rule at rho = 32, over 1 otherwise)
+    import ctypes
+    L = ctypes.CDLL(lib)
+    vp, u32, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
+    L.tri_ca_run.argtypes = [vp, vp, vp, u32, ctypes.c_size_t, u32, u32, i32, u32, u32, vp]
+    n, ld = 200, 208
+    span = (n - 1) * ld + n
+    a, b, c = 1 << 20, 1 << 24, 1 << 28  # 16-byte aligned, far apart: never dereferenced
+    life = (8, 12)
+    assert L.tri_ca_run(None, vp(b), vp(c), n, ld, *life, 0, 32, 3, None) == 1            # null in
+    assert L.tri_ca_run(vp(a), None, vp(c), n, ld, *life, 0, 32, 3, None) == 1            # null out
+    assert L.tri_ca_run(vp(a), vp(b), vp(c), 0, ld, *life, 0, 32, 3, None) == 1           # n = 0
+    assert L.tri_ca_run(vp(a), vp(b), vp(c), n, ld, *life, 0, 32, 0, None) == 1           # steps = 0
+    assert L.tri_ca_run(vp(a), vp(b), vp(c), n, ld, *life, 0, 12, 3, None) == 1           # rho 12
+    assert L.tri_ca_run(vp(a), vp(b), vp(c), n, 192, *life, 0, 32, 3, None) == 1          # ld < n
+    assert L.tri_ca_run(vp(a), vp(b), vp(c), n, 200, *life, 0, 32, 3, None) == 1          # ld % 16
+    assert L.tri_ca_run(vp(a + 4), vp(b), vp(c), n, ld, *life, 0, 32, 3, None) == 1       # misaligned in
+    assert L.tri_ca_run(vp(a), vp(b), vp(c), n, ld, 1 << 9, 12, 0, 32, 3, None) == 1      # birth past 8
+    assert L.tri_ca_run(vp(a), vp(b), vp(c), n, ld, *life, 4, 32, 3, None) == 1           # UTM
+    assert L.tri_ca_run(vp(a), vp(a + span - 16), vp(c), n, ld, *life, 0, 32, 3, None) == 1  # out overlaps in
+    assert L.tri_ca_run(vp(a), vp(b), None, n, ld, *life, 0, 32, 17, None) == 1           # 2 passes, no scratch
+    assert L.tri_ca_run(vp(a), vp(b), vp(b + 16), n, ld, *life, 0, 32, 17, None) == 1     # scratch overlaps out
+    assert L.tri_ca_run(vp(a), vp(b), None, n, ld, *life, 0, 16, 2, None) == 1            # rho 16 steps one at a time
+    assert L.tri_ca_run(vp(a), vp(b), None, n, ld, 8 | 64, 12, 0, 32, 2, None) == 1       # another rule, likewise
