@@ -2,8 +2,9 @@
 
 Section 3.1: the enumeration matrix D (Eq. eq_matrix_indexing), the closed
 form of lambda (Eq. eq_gmap), its worked examples, and the strict-triangle
-variant (Eq. eq_theorem_nodiag).  Section 6: tetrahedral numbers and the cubic
-whose root gives the layer of a block.
+variant (Eq. eq_theorem_nodiag).  Section 4.2: the upper-triangular map as
+printed, read 1-indexed.  Section 6: tetrahedral numbers and the cubic whose
+root gives the layer of a block.
 """
 import math
 import os
@@ -103,6 +104,37 @@ def test_improvement_bound():
         vals = [2.0 * m * m / (k * (m * m + m)) for m in (1, 10, 1000, 10 ** 6)]
         assert all(0 < v < 2 for v in vals)
         assert abs(vals[-1] - 2.0 / k) < 1e-5
+
+
+def _utm_printed(N: int, k: int):
+    # Section 4.2's upper-triangular map over N items, 1-indexed pairs a < b:
+    # a = floor(((2N + 1) - sqrt((2N - 1)^2 - 8k)) / 2), b = (a + 1) + k - (a - 1)(2N - a) / 2,
+    # evaluated exactly: floor((2N + 1 - sqrt(D)) / 2) = floor((2N + 1 - ceil(sqrt(D))) / 2)
+    # for integer D >= 0, since no integer lies strictly between sqrt(D) and its ceiling.
+    D = (2 * N - 1) ** 2 - 8 * k
+    r = math.isqrt(D)
+    c = r if r * r == D else r + 1
+    a = (2 * N + 1 - c) // 2
+    b = (a + 1) + k - (a - 1) * (2 * N - a) // 2
+    return a, b
+
+
+def test_utm_reading_hand_values_and_bijection():
+    # reading of Section 4.2: the printed formula is 1-indexed.  By hand for
+    # N = 4: k = 0 .. 5 -> (1,2), (1,3), (1,4), (2,3), (2,4), (3,4).
+    assert [_utm_printed(4, k) for k in range(6)] == [(1, 2), (1, 3), (1, 4), (2, 3), (2, 4), (3, 4)]
+    # over N items it enumerates every pair a < b once, row by row; with
+    # N = n + 1 and (i, j) = (b - 2, a - 1) that is the triangle 0 <= j <= i < n
+    for n in (1, 2, 3, 7, 64, 299):
+        N = n + 1
+        pairs = [_utm_printed(N, k) for k in range(N * (N - 1) // 2)]
+        assert pairs == [(a, b) for a in range(1, N + 1) for b in range(a + 1, N + 1)]
+        tri = sorted((b - 2, a - 1) for a, b in pairs)
+        assert tri == [(i, j) for i in range(n) for j in range(i + 1)]
+    # the last k gives the last pair
+    N = 10
+    a, b = _utm_printed(N, N * (N - 1) // 2 - 1)
+    assert (a, b) == (N - 1, N)
 
 
 @pytest.mark.parametrize("m", [1, 2, 5, 24])
