@@ -2,8 +2,9 @@
 
 Section 3.1: the enumeration matrix D (Eq. eq_matrix_indexing), the closed
 form of lambda (Eq. eq_gmap), its worked examples, and the strict-triangle
-variant (Eq. eq_theorem_nodiag).  Section 4.2: the upper-triangular map as
-printed, read 1-indexed.  Section 6: tetrahedral numbers and the cubic whose
+variant (Eq. eq_theorem_nodiag).  Section 4.2: the rectangular box and the
+recursive partition as read, and the upper-triangular map as printed, read
+1-indexed.  Section 6: tetrahedral numbers and the cubic whose
 root gives the layer of a block.
 """
 import math
@@ -135,6 +136,56 @@ def test_utm_reading_hand_values_and_bijection():
     N = 10
     a, b = _utm_printed(N, N * (N - 1) // 2 - 1)
     assert (a, b) == (N - 1, N)
+
+
+def _rb_blocks(m: int):
+    # reading of Section 4.2's rectangular box at block level: a grid of m
+    # columns and (m + 1) / 2 rows (odd m) or m / 2 + 1 rows (even m, whose last
+    # row is used only for t_x < m / 2); block (t_x, t_y) is (m - t_y - 1,
+    # m - t_x - 1) for t_x >= t_y and (t_y - 1, t_x) below.  Returns the used
+    # blocks and the grid's block count.
+    rows = (m + 1) // 2 if m % 2 else m // 2 + 1
+    used = []
+    for ty in range(rows):
+        for tx in range(m):
+            if m % 2 == 0 and ty == rows - 1 and tx >= m // 2:
+                continue
+            used.append((m - ty - 1, m - tx - 1) if tx >= ty else (ty - 1, tx))
+    return used, rows * m
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 7, 8, 33, 64, 101])
+def test_rb_reading_tiles_the_triangle(m):
+    used, launched = _rb_blocks(m)
+    assert sorted(used) == [(i, j) for i in range(m) for j in range(i + 1)]
+    # every grid block is used for odd m; even m wastes the last row's m / 2
+    assert launched - len(used) == (0 if m % 2 else m // 2)
+
+
+def _rec_blocks(k: int):
+    # reading of Section 4.2's recursive partition (details deferred by the
+    # paper): m = 2^k block rows; level 0 is the m diagonal blocks; level l =
+    # 1 .. k holds 2^(k - l) squares of side 2^(l - 1), square s covering block
+    # rows [s 2^l + 2^(l - 1), (s + 1) 2^l) and columns [s 2^l, s 2^l + 2^(l - 1)).
+    m = 1 << k
+    levels = [[(i, i) for i in range(m)]]
+    for lev in range(1, k + 1):
+        side, step = 1 << (lev - 1), 1 << lev
+        levels.append([(r, c) for s in range(m >> lev)
+                       for r in range(s * step + side, (s + 1) * step)
+                       for c in range(s * step, s * step + side)])
+    return m, levels
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 6])
+def test_rec_reading_tiles_the_triangle(k):
+    m, levels = _rec_blocks(k)
+    allb = [b for lev in levels for b in lev]
+    assert sorted(allb) == [(i, j) for i in range(m) for j in range(i + 1)]
+    # each level above the first has half the squares of the one below it
+    squares = [m >> lev for lev in range(1, k + 1)]
+    assert all(a == 2 * b for a, b in zip(squares, squares[1:]))
+    assert len(levels) == k + 1
 
 
 @pytest.mark.parametrize("m", [1, 2, 5, 24])
