@@ -771,7 +771,7 @@ def run_split(args, rank: int, world: int, local: int):
             x.copy_(xh, non_blocking=True)
             step()
             bh.copy_(band, non_blocking=True)
-        ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), 1)], world, dev)[0]
+        ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), args.warmup)], world, dev)[0]
         e2e = {"value": P / (ms_e2e * 1e-3), "ms_per_step": ms_e2e, "unit": "pairs/s",
                "h2d_bytes_per_step": xh.numel() * 4, "d2h_bytes_per_step": (pe - pb) * 4,
                "path": "copies around tri_edm_rows (each rank's band)"}
@@ -983,12 +983,14 @@ def main():
                   "fixup_ms": tot[2] / len(phase_events)}
 
     # ---- bounding box on the same input (the paper's I = t_BB / t_lambda)
-    ms_bb = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_BB), max(3, args.steps // 2), 2)
+    # (every timed leg warms up with the headline's W >= 3 steps)
+    ms_bb = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_BB), max(3, args.steps // 2), args.warmup)
     # ---- the FP32 direct-difference path on the same input, for comparison
     if prec == tri.FP32:
         ms_fp32 = ms_step
     else:
-        ms_fp32 = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_LAMBDA, tri.FP32), 3, 1)
+        ms_fp32 = float("nan") if args.no_arms else timed(lambda: step(tri.MAP_LAMBDA, tri.FP32), 3,
+                                                              args.warmup)
     ms_bb, ms_fp32 = max_over_ranks([ms_bb, ms_fp32], world, dev)
     # ---- the paper's comparison of maps at its own sizes (outside the timed region)
     paper = None if args.no_arms else paper_comparison(tri, inputs, dev, stream)
@@ -1044,7 +1046,7 @@ def main():
             def e2e_step():
                 tri.tri_edm_host(xh, oh, x, out, ws, map=tri.MAP_LAMBDA, prec=prec, n_flagged=flagged)
 
-        ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), 1)], world, dev)[0]
+        ms_e2e = max_over_ranks([timed(e2e_step, max(2, min(args.steps, 5)), args.warmup)], world, dev)[0]
         # the same steps one by one (the host link is shared with the machine's
         # other jobs: a slow step shows here rather than only in the mean)
         step_ms = []
@@ -1064,8 +1066,8 @@ def main():
         def banded():
             for a, b in zip(edges[:-1], edges[1:]):
                 oh[a:b].copy_(out[a:b], non_blocking=True)
-        ms_copy = timed(banded, 2, 1)
-        ms_copy1 = timed(lambda: oh.copy_(out, non_blocking=True), 2, 1)
+        ms_copy = timed(banded, 2, args.warmup)
+        ms_copy1 = timed(lambda: oh.copy_(out, non_blocking=True), 2, args.warmup)
         e2e = {"value": job_rate(world, P, ms_e2e), "ms_per_step": ms_e2e,
                "d2h_copy_alone_gbs": oh.numel() * 4 / (ms_copy * 1e-3) / 1e9,
                "d2h_single_copy_gbs": oh.numel() * 4 / (ms_copy1 * 1e-3) / 1e9,
