@@ -586,7 +586,10 @@ def run_suite(args):
               "speedup_over_step_by_step": 100 * t["lambda"] / tr["lambda"],
               "roofline": {"bound": "hbm", "achieved": gbs_run, "peak": hbm, "unit": "GB/s", "frac": gbs_run / hbm,
                            "algorithmic_bytes_per_pass": 2 * cells, "passes": passes,
-                           "note": "one read and one write of every cell per pass; the 16-cell halos are re-read"}})
+                           "note": "one read and one write of every cell per pass; the 16-cell halos are re-read; "
+                                   "the kernel is bound by its ALU pipe (ncu), not by these bytes"},
+              "cpu_baseline": cpu_leg(lambda: oracle.ca_run(gh, 4), 4 * cells, "cells/s",
+                                      "four steps of the n = 16384 grid")})
 
     if want("at"):
         # a7: Axilrod-Teller energy over the tetrahedral domain, N = 1536, rho = 16
